@@ -1,0 +1,105 @@
+"""Q1 (multilinear) finite elements on a uniform rectangular mesh, homogeneous Dirichlet.
+
+Section 2.1: V_h is the tensor product of 1D continuous piecewise-linear spaces with nodes
+x^j = a + j h, j = 0..N, and only the N-1 interior hat functions kept (eq. (2.4)).
+Section 4, eq. (4.1): the semi-discrete system is M dU/dt + K U = F with
+M = A_x (x) A_y (x) A_z, K = D (B_x (x) A_y (x) A_z + ...), A = (h/6) R, B = (1/h) G^D.
+
+Here A, B, M and K are assembled from element integrals (eq. (2.5) tested with every basis
+function), never from the Kronecker form; the Kronecker form is a pin in the tests.
+Parity: pinned (element integrals against Gauss quadrature of the hat functions; assembled
+matrices against eq. (4.1)).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def element_mass_1d(h: float) -> np.ndarray:
+    """Integrals of products of the two linear shape functions on an element of length h.
+
+    int_0^h (1 - s/h)^2 ds = h/3 and int_0^h (1 - s/h)(s/h) ds = h/6.
+    """
+    return np.array([[h / 3.0, h / 6.0], [h / 6.0, h / 3.0]])
+
+
+def element_stiffness_1d(h: float) -> np.ndarray:
+    """Integrals of products of the derivatives (-1/h and +1/h) of the two shape functions."""
+    return np.array([[1.0 / h, -1.0 / h], [-1.0 / h, 1.0 / h]])
+
+
+def assemble_1d(N: int, h: float) -> tuple[np.ndarray, np.ndarray]:
+    """Assemble the 1D mass A and stiffness B over N elements; keep the N-1 interior nodes.
+
+    Returns dense (N-1) x (N-1) matrices. Node j of element e is e + j (j = 0, 1).
+    """
+    if N < 2:
+        raise ValueError("need at least two intervals")
+    Af = np.zeros((N + 1, N + 1))
+    Bf = np.zeros((N + 1, N + 1))
+    me, ke = element_mass_1d(h), element_stiffness_1d(h)
+    for e in range(N):
+        for a in range(2):
+            for b in range(2):
+                Af[e + a, e + b] += me[a, b]
+                Bf[e + a, e + b] += ke[a, b]
+    return Af[1:N, 1:N].copy(), Bf[1:N, 1:N].copy()
+
+
+def element_matrices_nd(h: tuple, D: float) -> tuple[np.ndarray, np.ndarray]:
+    """Q1 element mass and stiffness in d dimensions (local nodes ordered x fastest).
+
+    The basis functions on an element are products of 1D shape functions, so each integral over
+    the element factorises into 1D integrals:
+      mass:      prod_a m_a[i_a, j_a]
+      stiffness: D * sum_a k_a[i_a, j_a] * prod_{b != a} m_b[i_b, j_b]   (bilinear form (2.3))
+    """
+    d = len(h)
+    m1 = [element_mass_1d(ha) for ha in h]
+    k1 = [element_stiffness_1d(ha) for ha in h]
+    nloc = 2 ** d
+    locs = [tuple((n >> a) & 1 for a in range(d)) for n in range(nloc)]  # a = 0 is x (fastest)
+    Me = np.zeros((nloc, nloc))
+    Ke = np.zeros((nloc, nloc))
+    for p, ip in enumerate(locs):
+        for q, iq in enumerate(locs):
+            Me[p, q] = np.prod([m1[a][ip[a], iq[a]] for a in range(d)])
+            Ke[p, q] = D * sum(
+                k1[a][ip[a], iq[a]] * np.prod([m1[b][ip[b], iq[b]] for b in range(d) if b != a])
+                for a in range(d))
+    return Me, Ke
+
+
+def assemble_global(N: tuple, h: tuple, D: float) -> tuple[sp.csr_matrix, sp.csr_matrix]:
+    """Assemble the global M and K over all Q1 elements; restrict to interior nodes.
+
+    N, h are per axis (x first). Interior unknowns are numbered x fastest, matching the array
+    layout (N_z-1, N_y-1, N_x-1) in C order.
+    """
+    d = len(N)
+    Me, Ke = element_matrices_nd(h, D)
+    full = [n + 1 for n in N]
+    strides = [int(np.prod(full[:a])) for a in range(d)]
+    rows, cols, mv, kv = [], [], [], []
+    locs = [tuple((n >> a) & 1 for a in range(d)) for n in range(2 ** d)]
+    for e in itertools.product(*[range(n) for n in reversed(N)]):
+        e = tuple(reversed(e))  # e[0] is the x element index
+        nodes = [sum((e[a] + lp[a]) * strides[a] for a in range(d)) for lp in locs]
+        for p in range(len(nodes)):
+            for q in range(len(nodes)):
+                rows.append(nodes[p])
+                cols.append(nodes[q])
+                mv.append(Me[p, q])
+                kv.append(Ke[p, q])
+    ntot = int(np.prod(full))
+    Mf = sp.coo_matrix((mv, (rows, cols)), shape=(ntot, ntot)).tocsr()
+    Kf = sp.coo_matrix((kv, (rows, cols)), shape=(ntot, ntot)).tocsr()
+    interior = []
+    for idx in itertools.product(*[range(1, n) for n in reversed(N)]):
+        idx = tuple(reversed(idx))
+        interior.append(sum(idx[a] * strides[a] for a in range(d)))
+    interior = np.array(interior)
+    return Mf[interior][:, interior].tocsr(), Kf[interior][:, interior].tocsr()

@@ -1,0 +1,90 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the bench and the oracle's tests.
+
+This module holds no arithmetic of the method itself: it only draws random numbers and states the
+workload shapes. Both sides (the CUDA library and the CPU oracle) receive the arrays made here.
+
+Generator: SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+OOPSLA 2014). Element ``i`` of a stream with seed ``s`` is ``mix(s + (i + 1) * GAMMA)`` (mod 2**64),
+so the stream is counter-based and can be produced in any order. The top 53 bits map to [0, 1).
+Fields are filled in index order with x fastest, i.e. a C-ordered array of shape
+``(N_z - 1, N_y - 1, N_x - 1)`` (3D) or ``(N_y - 1, N_x - 1)`` (2D).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+DEFAULT_SEED = 20220923
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Return ``count`` 64-bit outputs of SplitMix64 starting at stream position ``offset``."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed % (1 << 64)) + idx * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    z = splitmix64(seed, count, offset)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniform_field(shape: Sequence[int], lo: float, hi: float, seed: int) -> np.ndarray:
+    """Field of i.i.d. uniform(lo, hi) values, C order (x fastest), float64."""
+    n = int(np.prod(shape)) if len(shape) else 1
+    return (lo + (hi - lo) * uniform01(seed, n)).reshape(tuple(shape))
+
+
+def interior_shape(N: Sequence[int]) -> tuple:
+    """Array shape of the interior nodal unknowns for intervals ``N = (N_x, N_y[, N_z])``."""
+    return tuple(int(n) - 1 for n in reversed(N))
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One synthetic Allen-Cahn workload shaped like the paper's 2D/3D experiments."""
+
+    name: str
+    N: tuple            # intervals per axis (N_x, N_y[, N_z]); unit domain -> h = 1/N
+    D: float
+    tau: float
+    nsteps: int
+    scheme: int         # 1 = ETDRK1 (EIFE1), 2 = ETDRK2 (EIFE2)
+    u_lo: float
+    u_hi: float
+    seed: int = DEFAULT_SEED
+    dtypes: tuple = field(default=("f64",))
+
+    @property
+    def h(self) -> tuple:
+        return tuple(1.0 / n for n in self.N)
+
+    @property
+    def unknowns(self) -> int:
+        return int(np.prod(interior_shape(self.N)))
+
+    def u0(self) -> np.ndarray:
+        return uniform_field(interior_shape(self.N), self.u_lo, self.u_hi, self.seed)
+
+
+# The synthetic workloads (unit square/cube, homogeneous Dirichlet, f = u - u^3).
+AC2D_64 = Workload("allen_cahn_2d_64x64_D1e-2_tau1e-2_etdrk2", (64, 64), 1e-2, 1e-2, 100, 2,
+                   -0.9, 0.9, DEFAULT_SEED + 0, ("f64",))
+AC2D_1024 = Workload("allen_cahn_2d_1024x1024_D1e-4_tau5e-3_etdrk2", (1024, 1024), 1e-4, 5e-3, 2000, 2,
+                     -0.05, 0.05, DEFAULT_SEED + 1, ("f32", "f64"))
+AC3D_256 = Workload("allen_cahn_3d_256cubed_D1e-3_tau1e-2_etdrk2", (256, 256, 256), 1e-3, 1e-2, 500, 2,
+                    -0.9, 0.9, DEFAULT_SEED + 2, ("f32",))
+AC3D_64 = Workload("allen_cahn_3d_64cubed_D1e-3_tau1e-2_etdrk2", (64, 64, 64), 1e-3, 1e-2, 500, 2,
+                   -0.9, 0.9, DEFAULT_SEED + 2, ("f32", "f64"))
+
+WORKLOADS = {w.name: w for w in (AC2D_64, AC2D_1024, AC3D_256, AC3D_64)}
