@@ -1,0 +1,300 @@
+"""Throughput of the EIFE2 (ETDRK2) Q1 finite-element solve on GB300, one JSON line on stdout.
+
+A bench "step" is one full run of the workload: the 2D Allen-Cahn field on a 1024 x 1024 mesh
+(1023^2 interior unknowns, D = 1e-4, tau = 5e-3, FP32 transforms with FP64-derived tables) advanced
+by 2000 ETDRK2 time steps from its seeded synthetic u0, which is resident in HBM when timing starts.
+value = unknown-updates per second (unknowns x time steps / s) over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
+
+--impl reference times the CPU oracle (the plain FP64 NumPy implementation that the tests use as
+ground truth) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2209_11922_gb300 import inputs  # noqa: E402
+
+METRIC = "ETDRK2 unknown-updates/s"
+UNIT = "unknown-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, w):
+    """The CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    world, rank, _ = _dist_setup(args)
+    if rank != 0:
+        return 0
+    from oracle import etd as oetd
+    sample = args.ref_sample_steps
+    u0 = w.u0()
+    st = oetd.make_stepper(w.N, w.h, w.D, w.tau, w.scheme)
+    f = oetd.allen_cahn()
+    for _ in range(args.warmup):
+        st.run(u0, sample, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.run(u0, sample, f)
+    dt = time.perf_counter() - t0
+    value = w.unknowns * sample * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample": f"{sample} time steps of the {w.N} field per bench step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} ETDRK2 time steps of {w.name} per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(w, seconds: float = 15.0) -> dict:
+    """Time the oracle on the host cores for a bounded sample of the same workload."""
+    from oracle import etd as oetd
+    u0 = w.u0()
+    st = oetd.make_stepper(w.N, w.h, w.D, w.tau, w.scheme)
+    f = oetd.allen_cahn()
+    t0 = time.perf_counter()
+    st.run(u0, 1, f)
+    one = time.perf_counter() - t0
+    n = max(1, min(200, int(seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    st.run(u0, n, f)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1)))
+    return {"value": w.unknowns * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} ETDRK2 time steps of {w.name} (FP64 NumPy oracle, dense per-axis products)"}
+
+
+def run_gb300(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2209_11922_gb300.etd import Plan
+
+    world, rank, local = _dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dtype = args.dtype
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    nsteps = args.time_steps or w.nsteps
+    plan = Plan(w.N, w.D, w.tau, scheme=w.scheme, dtype=dtype)
+    info = plan.info()
+    u0 = torch.from_numpy(w.u0().astype(np.float32 if dtype == "f32" else np.float64)).cuda()
+    u = torch.empty_like(u0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_run():
+        u.copy_(u0)
+        flush.fill_(1.0)                         # evict L2 between bench steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(u, nsteps, stream)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            evs.append(one_run())
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    updates = float(w.unknowns) * nsteps * args.steps * world
+    value = updates / (ms_max * 1e-3)
+    nonfinite = plan.monitor(u)["nonfinite"]
+
+    # kernel-level timing of the same workload (separate run, events around every launch)
+    u.copy_(u0)
+    prof = plan.run_profiled(u, min(nsteps, 200), stream)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    step_kinds = {k: v for k, v in kinds.items() if k not in ("entry_exit", "pack", "monitor")}
+    dom = max(step_kinds, key=lambda k: step_kinds[k][0])
+    dom_ms, dom_n = step_kinds[dom]
+    rw = {"x_react": 2, "transform": 2, "stage1_etdrk2": 4, "stage2_etdrk2": 3, "stage_etdrk1": 3}[dom]
+    esz = 4 if dtype == "f32" else 8
+    alg_bytes = rw * w.unknowns * esz
+    achieved = alg_bytes / (dom_ms * 1e-3 / dom_n) / 1e9
+    peak, peak_src = _peaks()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(f"{w.name}:{dtype}:{dom}")
+        except Exception:
+            traffic = None
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hbuf = torch.empty(u0.shape, dtype=tdt, pin_memory=True).numpy()
+    u0h = u0.cpu().numpy()
+    for _ in range(max(1, args.warmup)):
+        hbuf[...] = u0h
+        plan.run_host(hbuf, nsteps)
+    e2e_t = 0.0
+    for _ in range(args.steps):
+        hbuf[...] = u0h
+        t0 = time.perf_counter()
+        plan.run_host(hbuf, nsteps)
+        e2e_t += time.perf_counter() - t0
+    e2e_val = float(w.unknowns) * nsteps * args.steps / e2e_t
+    if world > 1:
+        t = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        e2e_val = float(t.item()) * world
+
+    if rank == 0:
+        clocks = clk.summary()
+        entry_exit = 2 if len(w.N) == 2 else 4   # entry + exit launches per run
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": w.name, "mesh": list(w.N), "unknowns": w.unknowns, "time_steps_per_step": nsteps,
+                       "D": w.D, "tau": w.tau, "scheme": "ETDRK2" if w.scheme == 2 else "ETDRK1",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MiB buffer written between bench steps; within one run the fields stay L2-resident",
+                       "kernels_per_time_step": info["kernels_per_step"],
+                       "ms_per_time_step": ms_max / args.steps / nsteps},
+            "gpu_launches": args.steps * (info["kernels_per_step"] * nsteps + entry_exit),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": dom_ms / dom_n,
+                         "timing": "CUDA events around every launch of a separate profiled run"},
+            "pass_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in kinds.items()},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": w.unknowns * esz,
+                    "d2h_bytes_per_step": w.unknowns * esz},
+            "clocks": clocks,
+            "nonfinite": nonfinite,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    plan.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=inputs.AC2D_1024.name, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time-step count")
+    ap.add_argument("--ref-sample-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_gb300(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,143 @@
+/*
+ * etd.h - C ABI of the GB300 (sm_103a) exponential-integrator Q1 finite-element solver.
+ *
+ * Problem (Section 1, eq. (1.1); Section 2, eq. (2.1)): u_t = D Lap u + f(u) on a rectangle in 2D or
+ * 3D with homogeneous Dirichlet data, f(u) = flin * u + fcub * u^3 (Allen-Cahn: flin = 1,
+ * fcub = -1), applied to nodal values (the tensor F of Section 4 read as F = M f(U)).
+ * Space: Q1 (multilinear) elements on a uniform mesh with N_a intervals of size h_a per axis
+ * (Section 2.1); the unknowns are the (N_x-1)(N_y-1)[(N_z-1)] interior nodal values.
+ * Time: one EIFE1 step, eq. (2.13) (ETDRK1), or one EIFE2 step, eq. (2.14) with c_1 = 0 and
+ * c_2 in (0, 1] (ETDRK2; the paper's experiments use c_2 = 1/2, Section 5).
+ * Fast solve (Section 4): A_a = (h_a/6) R and B_a = (1/h_a) G^D share the orthonormal sine basis
+ * S_a = sqrt(2/N_a) sin(i j pi / N_a), so each step is a forward DST-I along every axis, a per-mode
+ * scaling by phi-functions of -tau D (mu_x,i + mu_y,j [+ mu_z,k]) with
+ * mu_a,i = (6/h_a^2)(1 - cos(i pi/N_a))/(2 + cos(i pi/N_a)), and inverse DST-I along every axis.
+ *
+ * Conventions for every entry point:
+ *  - A field `u` is the array of interior nodal values, x fastest (C order
+ *    [N_z-1][N_y-1][N_x-1] or [N_y-1][N_x-1]), dense, element type per etd_options.dtype.
+ *  - Device pointers are CUDA device (or managed) memory owned by the caller; the plan never frees
+ *    them. `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Calls enqueue work asynchronously on `stream` unless stated; they return before the GPU work
+ *    completes. Errors found on the host are returned before any GPU work is enqueued.
+ *  - No call aborts, traps or exits. Every call returns an etd_status; etd_last_error() gives a
+ *    human-readable detail for the calling thread's most recent failure.
+ *  - A plan is not thread-safe: use one plan per host thread, or serialise calls.
+ */
+#ifndef ETD_GB300_H
+#define ETD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct etd_plan_s* etd_plan;   /* opaque; owned by the library, released by etd_destroy */
+
+typedef enum {
+  ETD_OK = 0,
+  ETD_ERR_INVALID_ARG = 1,   /* a contract violation detected on the host; nothing was enqueued */
+  ETD_ERR_UNSUPPORTED = 2,   /* valid request this build cannot run (e.g. an axis length it has no kernel for) */
+  ETD_ERR_CUDA = 3,          /* a CUDA runtime call failed; see etd_last_error() */
+  ETD_ERR_OOM = 4,           /* device or pinned-host allocation failed */
+  ETD_ERR_NONFINITE = 5      /* etd_monitor found NaN/Inf values in the field */
+} etd_status;
+
+typedef enum { ETD_ETDRK1 = 1, ETD_ETDRK2 = 2 } etd_scheme;   /* EIFE1 eq. (2.13), EIFE2 eq. (2.14) */
+typedef enum { ETD_F64 = 0, ETD_F32 = 1 } etd_dtype;            /* arithmetic and storage type of u */
+typedef enum { ETD_ROUTE_AUTO = 0, ETD_ROUTE_FFT = 1 } etd_route; /* transform implementation */
+
+typedef struct {
+  etd_dtype dtype;   /* default ETD_F64 */
+  etd_route route;   /* default ETD_ROUTE_AUTO (the DST-I by FFT kernels) */
+  double c2;         /* EIFE2 stage node c_2 in (0, 1]; default 0.5 (Section 5) */
+  double flin;       /* f(u) = flin*u + fcub*u^3; defaults 1 and -1 (Allen-Cahn) */
+  double fcub;
+} etd_options;
+
+/* Fill *opt with the defaults above. Returns ETD_ERR_INVALID_ARG if opt is NULL. */
+etd_status etd_options_default(etd_options* opt);
+
+/*
+ * Create a plan for `ndim` in {2, 3} axes with N[a] intervals (N[0] = N_x, the fastest axis) of
+ * size h[a] > 0, diffusion D > 0 and time step tau > 0 (Section 2.2, uniform tau_n = tau).
+ * Allocates the device workspace (five fields of N_x*N_y[*N_z] elements) and the FP64-derived
+ * tables (eigenvalues mu_a, exp(-tau D mu_a), exp(-c2 tau D mu_a), twiddles) on the current
+ * device, and uploads them. Supported N[a]: 2^k (4..2048) and 3*2^k (6..1536).
+ * opt may be NULL (defaults). On success *out receives the plan.
+ * Errors: ETD_ERR_INVALID_ARG (out/N/h NULL, ndim not 2 or 3, N[a] < 2 or odd, h <= 0, D <= 0,
+ * tau <= 0, c2 outside (0, 1], non-finite values), ETD_ERR_UNSUPPORTED (N[a] without a kernel),
+ * ETD_ERR_OOM, ETD_ERR_CUDA.
+ */
+etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const double* h, double D,
+                           double tau, etd_scheme scheme, const etd_options* opt);
+
+/* Advance the device field u (in place) by `nsteps` >= 0 time steps on `stream`. nsteps = 0 is a
+ * no-op. Equivalent to nsteps calls of etd_step up to rounding (the internal state between steps
+ * stays spectral along all axes but the last). Errors: ETD_ERR_INVALID_ARG (plan or u NULL,
+ * nsteps < 0), ETD_ERR_CUDA. */
+etd_status etd_run(etd_plan plan, void* u, int64_t nsteps, void* stream);
+
+/* One time step: etd_run(plan, u, 1, stream). */
+etd_status etd_step(etd_plan plan, void* u, void* stream);
+
+/* Same as etd_run, but u_host is HOST memory (pinned or pageable) of the field's size: the call
+ * copies it to a plan-owned device buffer, runs, copies the result back and synchronises the
+ * stream before returning. */
+etd_status etd_run_host(etd_plan plan, void* u_host, int64_t nsteps, void* stream);
+
+/* Apply the orthonormal DST-I S_a along paper axis `axis` (0 = x, 1 = y, 2 = z) to the dense device
+ * field `in`, writing the dense device field `out` (may equal `in`). S_a is symmetric and its own
+ * inverse, so this is both the forward transform U~ = S^T (x)_a U of Section 4 and its inverse. */
+etd_status etd_apply_dst(etd_plan plan, int axis, const void* in, void* out, void* stream);
+
+typedef struct {
+  double mass;       /* 1^T M U with M the Q1 mass matrix */
+  double energy;     /* 1/2 U^T K U + sum_nodes prod(h) (u^2 - 1)^2 / 4 */
+  double maxabs;     /* max |u| */
+  int64_t nonfinite; /* number of NaN/Inf values */
+} etd_monitors;
+
+/* FP64 reductions over the device field u; synchronises `stream` and writes *out.
+ * Returns ETD_ERR_NONFINITE (with *out filled) when u holds NaN or Inf values. */
+etd_status etd_monitor(etd_plan plan, const void* u, etd_monitors* out, void* stream);
+
+/* Kernel-level timing of one etd_run: records CUDA events around every kernel launch, runs
+ * `nsteps` steps on `stream`, synchronises, and writes per pass kind the summed duration in
+ * milliseconds and the launch count (arrays of length ETD_NUM_PASS_KINDS). Not for production
+ * use: the events add launch overhead. */
+#define ETD_NUM_PASS_KINDS 8
+etd_status etd_run_profiled(etd_plan plan, void* u, int64_t nsteps, void* stream,
+                            double* ms_per_kind, int64_t* launches_per_kind);
+
+typedef struct {
+  int ndim;
+  int64_t N[3];
+  int64_t unknowns;            /* prod (N_a - 1) */
+  int64_t workspace_bytes;     /* device bytes owned by the plan */
+  int kernels_per_step;        /* kernel launches per time step in etd_run */
+  double bytes_per_step;       /* algorithmic HBM bytes per time step (field passes x size) */
+  int dtype;
+  int scheme;
+} etd_plan_info;
+
+/* Describe a plan. */
+etd_status etd_get_plan_info(etd_plan plan, etd_plan_info* info);
+
+/* Name of pass kind k (0 <= k < ETD_NUM_PASS_KINDS), or NULL. */
+const char* etd_pass_kind_name(int k);
+
+/* Release the plan's device memory and graphs. NULL is accepted. */
+etd_status etd_destroy(etd_plan plan);
+
+/* Static description of a status code. */
+const char* etd_status_string(etd_status s);
+
+/* Detail of the calling thread's most recent failure ("" if none). */
+const char* etd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ETD_GB300_H */

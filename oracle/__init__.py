@@ -17,6 +17,7 @@ Everything is FP64 NumPy/SciPy, written for readability, not speed:
 * ``etd``      the EIFE1 step, eq. (2.13), and the EIFE2 step, eq. (2.14), in the spectral form of
                eqs. (4.2)-(4.4), with dense per-axis products (tensor mode products of Section 4).
 * ``monitors`` mass 1^T M U, the discrete energy, max|u|.
+* ``transforms`` the orthonormal DST-I of one axis from its definition (kernel-level parity).
 
 Readings of the paper taken here (each one is listed with its evidence in the design doc):
 
@@ -30,4 +31,4 @@ Readings of the paper taken here (each one is listed with its evidence in DESIGN
 Parity status of each function is stated in its docstring; functions without an independent pin
 say "parity unpinned".
 """
-from . import fem, spectral, phi, etd, monitors  # noqa: F401
+from . import fem, spectral, phi, etd, monitors, transforms  # noqa: F401

@@ -1,0 +1,24 @@
+"""The orthonormal DST-I along one axis, written from its definition (Section 4).
+
+S_ij = sqrt(2/N) sin(i j pi / N), i, j = 1..N-1 (the sine matrix P of Section 4 scaled to be
+orthonormal, reading c-1 in the design doc); S is symmetric and S S = I, so it is both the forward
+transform U~ = S^T (x)_a U and its inverse. Applied as a dense product along the axis.
+Parity: pinned (equals, up to sign, the numerically computed eigenvectors of A and B; S S = I).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .etd import mode_product
+
+
+def sine_matrix(N: int) -> np.ndarray:
+    i = np.arange(1, N)
+    return np.sqrt(2.0 / N) * np.sin(np.outer(i, i) * np.pi / N)
+
+
+def dst_axis(U: np.ndarray, axis: int) -> np.ndarray:
+    """S (x)_axis U for paper axis ``axis`` (0 = x, the last array axis)."""
+    U = np.asarray(U, dtype=np.float64)
+    N = U.shape[U.ndim - 1 - axis] + 1
+    return mode_product(sine_matrix(N), U, axis)

@@ -1,0 +1,326 @@
+// dst_engine.cuh - orthonormal DST-I of many pencils, as used by the fast solve of Section 4.
+//
+// The transform applied along one axis of length N (N-1 interior nodes) is
+//     F_k = sqrt(2/N) * sum_{j=1}^{N-1} x_j sin(pi j k / N),  k = 1..N-1,
+// i.e. S = sqrt(2/N) P with the sine matrix P of Section 4 (S is symmetric and S^2 = I, so the
+// same routine is the forward transform and its inverse; Section 4 states the DST/iDST per axis).
+//
+// Algorithm (two real pencils a, b packed as one complex sequence c_j = a_j + i b_j):
+//   1. y_j = sin(pi j/N)(c_j + c_{N-j}) + (c_j - c_{N-j})/2 for j = 1..N-1, y_0 = 0.
+//   2. Z = length-N complex DFT of y with kernel exp(+2 pi i j k / N), computed by Stockham passes
+//      whose butterflies (radix R <= 32) run in registers; one shared-memory exchange per pass.
+//   3. With Y^a, Y^b the real DFTs separated from Z: F_{2k} = Im Y_k and
+//      F_{2k+1} = F_{2k-1} + Re Y_k (F_1 = Re Y_0 / 2), i.e. even outputs are
+//      (-i/2)(Z_k - Z_{N-k}) and odd outputs are half a prefix sum of G_0 = Z_0,
+//      G_m = Z_m + Z_{N-m}; the prefix sum runs per thread then across lanes by warp shuffles.
+// The identities in step 1 and 3 follow from splitting y into its even and odd parts about N/2.
+//
+// Layout: one pair occupies LP complex slots of shared memory; position j lives at
+// j + j / PADG (one padding slot every PADG entries) so that the strided writes of the first pass
+// hit distinct banks. Slot 0 holds position 0, which is the boundary node / mode 0 and is 0.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace etd {
+
+template <class T> struct Cx { T x, y; };
+
+template <class T> __device__ __forceinline__ Cx<T> operator+(Cx<T> a, Cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __device__ __forceinline__ Cx<T> operator-(Cx<T> a, Cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <class T> __device__ __forceinline__ Cx<T> operator*(T s, Cx<T> a) { return {s * a.x, s * a.y}; }
+template <class T> __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T> __device__ __forceinline__ Cx<T> mul_i(Cx<T> a) { return {-a.y, a.x}; }
+
+// cos(2 pi m / 96) for 0 <= m <= 24 (quarter wave), then by symmetry for any m >= 0.
+__host__ __device__ constexpr double qcos96(int m) {
+  switch (m) {
+    case 0: return 1.0;
+    case 1: return 0.9978589232386035;
+    case 2: return 0.9914448613738104;
+    case 3: return 0.9807852804032304;
+    case 4: return 0.9659258262890683;
+    case 5: return 0.9469301294951057;
+    case 6: return 0.9238795325112867;
+    case 7: return 0.8968727415326883;
+    case 8: return 0.8660254037844386;
+    case 9: return 0.8314696123025452;
+    case 10: return 0.7933533402912352;
+    case 11: return 0.7518398074789774;
+    case 12: return 0.7071067811865476;
+    case 13: return 0.6593458151000688;
+    case 14: return 0.6087614290087207;
+    case 15: return 0.5555702330196022;
+    case 16: return 0.5;
+    case 17: return 0.4422886902190013;
+    case 18: return 0.3826834323650898;
+    case 19: return 0.3214394653031616;
+    case 20: return 0.25881904510252074;
+    case 21: return 0.19509032201612828;
+    case 22: return 0.1305261922200516;
+    case 23: return 0.06540312923014306;
+    default: return 0.0;  // m == 24
+  }
+}
+__host__ __device__ constexpr double cos96(int m) {
+  m %= 96;
+  return m <= 24 ? qcos96(m) : m <= 48 ? -qcos96(48 - m) : m <= 72 ? -qcos96(m - 48) : qcos96(96 - m);
+}
+__host__ __device__ constexpr double sin96(int m) { return cos96((m % 96) + 72); }  // sin t = cos(t - pi/2)
+
+// v * exp(2 pi i m / 96); m is a compile-time constant after unrolling, so the trivial cases fold.
+template <class T> __device__ __forceinline__ Cx<T> twmul96(Cx<T> v, int m) {
+  m %= 96;
+  if (m == 0) return v;
+  if (m == 24) return {-v.y, v.x};
+  if (m == 48) return {-v.x, -v.y};
+  if (m == 72) return {v.y, -v.x};
+  const T c = (T)cos96(m), s = (T)sin96(m);
+  return {c * v.x - s * v.y, c * v.y + s * v.x};
+}
+
+// In-register DFT of length R with kernel exp(+2 pi i r k / R), natural order in and out.
+template <class T, int R> struct Dft {
+  static_assert(96 % R == 0, "radix must divide 96");
+  static constexpr int F = (R % 4 == 0) ? 4 : (R % 2 == 0 ? 2 : 3);
+  static constexpr int Q = R / F;
+  static __device__ __forceinline__ void run(Cx<T>* x);
+};
+template <class T> struct Dft<T, 1> { static __device__ __forceinline__ void run(Cx<T>*) {} };
+template <class T> struct Dft<T, 2> {
+  static __device__ __forceinline__ void run(Cx<T>* x) {
+    const Cx<T> a = x[0], b = x[1];
+    x[0] = a + b;
+    x[1] = a - b;
+  }
+};
+template <class T> struct Dft<T, 3> {
+  static __device__ __forceinline__ void run(Cx<T>* x) {
+    const Cx<T> s = x[1] + x[2], d = x[1] - x[2];
+    const Cx<T> t = x[0] - T(0.5) * s;
+    const Cx<T> u = mul_i(T(0.86602540378443864676) * d);
+    x[0] = x[0] + s;
+    x[1] = t + u;
+    x[2] = t - u;
+  }
+};
+template <class T> struct Dft<T, 4> {
+  static __device__ __forceinline__ void run(Cx<T>* x) {
+    const Cx<T> a0 = x[0] + x[2], a1 = x[0] - x[2], b0 = x[1] + x[3], b1 = mul_i(x[1] - x[3]);
+    x[0] = a0 + b0;
+    x[2] = a0 - b0;
+    x[1] = a1 + b1;
+    x[3] = a1 - b1;
+  }
+};
+template <class T, int R>
+__device__ __forceinline__ void Dft<T, R>::run(Cx<T>* x) {
+  Cx<T> y[F][Q];
+#pragma unroll
+  for (int s = 0; s < F; ++s)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) y[s][q] = x[F * q + s];
+#pragma unroll
+  for (int s = 0; s < F; ++s) Dft<T, Q>::run(y[s]);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    Cx<T> a[F];
+#pragma unroll
+    for (int s = 0; s < F; ++s) a[s] = twmul96(y[s][k], (96 / R) * s * k);
+    Dft<T, F>::run(a);
+#pragma unroll
+    for (int t = 0; t < F; ++t) x[k + Q * t] = a[t];
+  }
+}
+
+// Per-(type, N) pass plan: radices of the Stockham passes and threads per pair (TPP).
+// A thread holds at most 32 (FP32) / 16 (FP64) complex values in a pass.
+template <int... Rs> struct Radices {};
+template <class T, int N> struct FftPlan;
+#define ETD_PLAN(TYPE, NN, TPP_, ...)                      \
+  template <> struct FftPlan<TYPE, NN> {                   \
+    static constexpr int TPP = TPP_;                       \
+    using R = Radices<__VA_ARGS__>;                        \
+  };
+// powers of two
+ETD_PLAN(float, 4, 1, 4)
+ETD_PLAN(float, 8, 2, 4, 2)
+ETD_PLAN(float, 16, 4, 4, 4)
+ETD_PLAN(float, 32, 4, 8, 4)
+ETD_PLAN(float, 64, 8, 8, 8)
+ETD_PLAN(float, 128, 8, 16, 8)
+ETD_PLAN(float, 256, 16, 16, 16)
+ETD_PLAN(float, 512, 16, 32, 16)
+ETD_PLAN(float, 1024, 32, 32, 32)
+ETD_PLAN(float, 2048, 64, 16, 8, 16)
+ETD_PLAN(double, 4, 1, 4)
+ETD_PLAN(double, 8, 2, 4, 2)
+ETD_PLAN(double, 16, 4, 4, 4)
+ETD_PLAN(double, 32, 4, 8, 4)
+ETD_PLAN(double, 64, 8, 8, 8)
+ETD_PLAN(double, 128, 8, 16, 8)
+ETD_PLAN(double, 256, 16, 16, 16)
+ETD_PLAN(double, 512, 32, 8, 8, 8)
+ETD_PLAN(double, 1024, 64, 16, 8, 8)
+ETD_PLAN(double, 2048, 128, 16, 16, 8)
+// three times a power of two
+ETD_PLAN(float, 6, 1, 6)
+ETD_PLAN(float, 12, 2, 4, 3)
+ETD_PLAN(float, 24, 4, 8, 3)
+ETD_PLAN(float, 48, 4, 12, 4)
+ETD_PLAN(float, 96, 8, 12, 8)
+ETD_PLAN(float, 192, 16, 12, 16)
+ETD_PLAN(float, 384, 32, 12, 32)
+ETD_PLAN(float, 768, 32, 24, 32)
+ETD_PLAN(float, 1536, 64, 16, 3, 32)
+ETD_PLAN(double, 6, 1, 6)
+ETD_PLAN(double, 12, 2, 4, 3)
+ETD_PLAN(double, 24, 4, 8, 3)
+ETD_PLAN(double, 48, 4, 12, 4)
+ETD_PLAN(double, 96, 8, 12, 8)
+ETD_PLAN(double, 192, 16, 12, 16)
+ETD_PLAN(double, 384, 32, 8, 3, 16)
+ETD_PLAN(double, 768, 64, 16, 3, 16)
+ETD_PLAN(double, 1536, 128, 16, 6, 16)
+#undef ETD_PLAN
+
+template <class L> struct FirstRadix;
+template <int R0, int... Rs> struct FirstRadix<Radices<R0, Rs...>> { static constexpr int value = R0; };
+
+template <class T, int N> struct PairLayout {
+  static constexpr int TPP = FftPlan<T, N>::TPP;
+  static constexpr int PADG = FirstRadix<typename FftPlan<T, N>::R>::value;
+  static constexpr int LP = N + N / PADG + 1;  // complex slots per pair
+  static __device__ __forceinline__ int at(int j) { return j + j / PADG; }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Stockham passes. Pass with radix R after Ns points are already combined: butterfly jj reads
+// positions jj + r*N/R, twiddles by w_N^{(jj mod Ns) r N/(Ns R)}, and writes
+// (jj/Ns)*Ns*R + (jj mod Ns) + r*Ns. In place: all reads, barrier, all writes, barrier.
+// The first pass folds in step 1 (pre-processing of the DST).
+template <class T, int N, int NS, bool FIRST, int R, int... Rest>
+__device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
+                                         const T* __restrict__ sn, int l) {
+  using L = PairLayout<T, N>;
+  constexpr int TPP = L::TPP;
+  constexpr int TP = N / R;
+  constexpr int QN = (TP + TPP - 1) / TPP;
+  Cx<T> v[QN][R];
+#pragma unroll
+  for (int q = 0; q < QN; ++q) {
+    const int jj = l + TPP * q;
+    if (TP % TPP == 0 || jj < TP) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int idx = jj + r * TP;
+        Cx<T> xv;
+        if (FIRST) {
+          if (r == 0 && jj == 0) {
+            xv = {T(0), T(0)};
+          } else {
+            const Cx<T> c = bp[L::at(idx)], d = bp[L::at(N - idx)];
+            const T s = sn[idx];
+            xv = s * (c + d) + T(0.5) * (c - d);
+          }
+        } else {
+          xv = bp[L::at(idx)];
+        }
+        if (NS > 1 && r > 0) xv = cmul(xv, tw[(jj % NS) * r * (N / (NS * R))]);
+        v[q][r] = xv;
+      }
+      Dft<T, R>::run(v[q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < QN; ++q) {
+    const int jj = l + TPP * q;
+    if (TP % TPP == 0 || jj < TP) {
+      const int base = (jj / NS) * NS * R + (jj % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) bp[L::at(base + r * NS)] = v[q][r];
+    }
+  }
+  __syncthreads();
+  if constexpr (sizeof...(Rest) > 0) stockham<T, N, NS * R, false, Rest...>(bp, tw, sn, l);
+}
+
+template <class T, int N, int... Rs>
+__device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, Radices<Rs...>) {
+  stockham<T, N, 1, true, Rs...>(bp, tw, sn, l);
+}
+
+// `mask` names the lanes of the warp that exist (a CTA may have fewer than 32 threads).
+template <class T>
+__device__ __forceinline__ Cx<T> shfl_up_cx(unsigned mask, Cx<T> v, int d, int width) {
+  return {__shfl_up_sync(mask, v.x, d, width), __shfl_up_sync(mask, v.y, d, width)};
+}
+
+// Full DST-I of the pair at bp (in place); sc = sqrt(2/N)/2. `epi(j, w)` receives the scaled
+// result w at position j
+// (j = 0..N-1, w = 0 at j = 0) after every read of the pair has completed, and returns the value
+// stored at j; it may also read or write other buffers at the same (pair, j).
+// `scr` is shared scratch of TPP/32 complex per pair (used only when TPP > 32).
+template <class T, int N, class Epi>
+__device__ __forceinline__ void dst_pair(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
+                                         const T* __restrict__ sn, int l, Cx<T>* scr, T sc, Epi&& epi) {
+  using L = PairLayout<T, N>;
+  constexpr int TPP = L::TPP;
+  constexpr int C = (N / 2) / TPP;
+  static_assert(C * TPP == N / 2, "N/2 must be a multiple of the threads per pair");
+  run_fft<T, N>(bp, tw, sn, l, typename FftPlan<T, N>::R{});
+
+  Cx<T> g[C], e[C];
+#pragma unroll
+  for (int i = 0; i < C; ++i) {
+    const int m = l * C + i;
+    const Cx<T> zm = bp[L::at(m)];
+    if (m == 0) {
+      g[i] = zm;
+      e[i] = {T(0), T(0)};
+    } else {
+      const Cx<T> zn = bp[L::at(N - m)];
+      g[i] = zm + zn;
+      const Cx<T> d = zm - zn;
+      e[i] = {d.y, -d.x};
+    }
+    if (i > 0) g[i] = g[i] + g[i - 1];
+  }
+  // exclusive offset of this lane's chunk within the pair
+  constexpr int W = TPP < 32 ? TPP : 32;
+  const Cx<T> tot = g[C - 1];
+  Cx<T> inc = tot;
+  const int ls = l % W;
+  const unsigned mask = __activemask();  // every thread of the CTA reaches this point converged
+#pragma unroll
+  for (int d = 1; d < W; d <<= 1) {
+    const Cx<T> t = shfl_up_cx(mask, inc, d, W);
+    if (ls >= d) inc = inc + t;
+  }
+  if constexpr (TPP > 32) {
+    constexpr int NW = TPP / 32;
+    const int w = l / 32;
+    if (ls == 31) scr[w] = inc;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NW - 1; ++k)
+      if (k < w) inc = inc + scr[k];
+  } else {
+    __syncthreads();
+  }
+  const Cx<T> off = inc - tot;
+#pragma unroll
+  for (int i = 0; i < C; ++i) {
+    const int m = l * C + i;
+    const Cx<T> w0 = (m == 0) ? Cx<T>{T(0), T(0)} : sc * e[i];
+    const Cx<T> w1 = sc * (g[i] + off);
+    bp[L::at(2 * m)] = epi(2 * m, w0);
+    bp[L::at(2 * m + 1)] = epi(2 * m + 1, w1);
+  }
+  __syncthreads();
+}
+
+}  // namespace etd

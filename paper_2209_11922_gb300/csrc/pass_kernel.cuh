@@ -1,0 +1,339 @@
+// pass_kernel.cuh - one "axis pass" of the fast EIFE solve (Section 4): a CTA stages a tile of
+// pencils of one axis in shared memory, runs a short program of DST-I transforms with fused
+// pointwise epilogues, and writes the tile back.
+//
+// Pencil pairs: along x (contiguous rows) a pair is two adjacent rows; along y or z (strided) a
+// pair is two adjacent x-columns, so each row segment of the tile is already a complex pair.
+//
+// Ops and what they compute (U physical, ~ spectral along the transformed axes):
+//   ENTRY     dense u -> pitched field, DST along x                              (x)
+//   EXIT      DST along x -> dense u                                             (x)
+//   PACK/UNPACK  dense <-> pitched without transform                             (x)
+//   REACT     DST, nodal reaction f(u) = flin u + fcub u^3, DST                  (x)
+//   TRANSFORM DST                                                                (any axis)
+//   RK1       last axis: DST(U), DST(N0), U~+ = e^{-z} U~ + tau phi1(-z) N0~, DST  -> eq. (2.13)
+//   S1        last axis: DST(U), DST(N0), U2~ = e^{-c2 z} U~ + c2 tau phi1(-c2 z) N0~ (DST -> out0),
+//             P = e^{-z} U~ + tau (phi1 - phi2/c2)(-z) N0~ (-> out1)               -> eq. (2.14)
+//   S2        last axis: DST(N2), U~+ = P + tau/c2 phi2(-z) N2~, DST               -> eq. (2.14)
+// with z = tau D (mu_x + mu_y [+ mu_z]) per mode (the tensor H of Section 4 times tau).
+#pragma once
+#include "dst_engine.cuh"
+
+namespace etd {
+
+enum PassOp : int {
+  OP_ENTRY = 0,
+  OP_EXIT = 1,
+  OP_REACT = 2,
+  OP_TRANSFORM = 3,
+  OP_RK1 = 4,
+  OP_S1 = 5,
+  OP_S2 = 6,
+  OP_PACK = 7,
+  OP_UNPACK = 8,
+};
+
+enum EpiKind : int { EPI_PLAIN = 0, EPI_REACT = 1, EPI_RK1 = 2, EPI_S1 = 3, EPI_S2 = 4 };
+
+template <class T> struct PassArgs {
+  int op, axis, ndim;
+  int nx, ny, nz;   // pitched extents; nz = 1 in 2D. Index 0 of each axis is the boundary / mode 0.
+  int P;            // pencil pairs per CTA
+  int tiles_x;      // strided passes: nx / (2P)
+  int npairs;       // contiguous passes: ny * nz / 2
+  const T* in0;
+  const T* in1;
+  T* out0;
+  T* out1;
+  const T* tw;      // exp(2 pi i m / N), m < N, interleaved (re, im), of the transformed axis
+  const T* sn;      // sin(pi j / N), j < N
+  const T* zeta[3]; // per paper axis: tau D mu_a
+  const T* ex[3];   // exp(-tau D mu_a)
+  const T* ec[3];   // exp(-c2 tau D mu_a)
+  T sc, tau, c2, flin, fcub;
+};
+
+__host__ __device__ constexpr double inv_factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= (double)k;
+  return 1.0 / f;
+}
+
+// phi_2(z) = sum_{m>=0} z^m / (m+2)! by Horner, for |z| < 1 (truncation below the type's epsilon).
+template <class T> __device__ __forceinline__ T phi2_series(T z) {
+  constexpr int M = sizeof(T) == 4 ? 10 : 18;
+  T p = (T)inv_factorial(M + 1);
+#pragma unroll
+  for (int m = M - 2; m >= 0; --m) p = p * z + (T)inv_factorial(m + 2);
+  return p;
+}
+
+// phi_1(-zeta), phi_2(-zeta) for zeta >= 0 with E = exp(-zeta): series for zeta < 1, else the
+// recurrence phi_{k+1} = (phi_k - 1/k!)/z, which has no cancellation there.
+template <class T> __device__ __forceinline__ void phi12(T zeta, T E, T& p1, T& p2) {
+  if (zeta < T(1)) {
+    p2 = phi2_series<T>(-zeta);
+    p1 = T(1) - zeta * p2;
+  } else {
+    p1 = (T(1) - E) / zeta;
+    p2 = (T(1) - p1) / zeta;
+  }
+}
+template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E) {
+  if (zeta < T(1)) return T(1) - zeta * phi2_series<T>(-zeta);
+  return (T(1) - E) / zeta;
+}
+
+template <class T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+template <class T, int N>
+__global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> A) {
+  using L = PairLayout<T, N>;
+  using C = Cx<T>;
+  using VT = typename V2<T>::type;
+  constexpr int TPP = L::TPP;
+  constexpr int LP = L::LP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const C* __restrict__ tw = reinterpret_cast<const C*>(A.tw);
+  const T* __restrict__ sn = A.sn;
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  const int op = A.op;
+  const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
+  C* b1 = b0 + A.P * LP;
+  C* scr = b0 + (two ? 2 : 1) * A.P * LP;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int P = A.P;
+  const int p = tid / TPP, l = tid % TPP;
+  const bool contiguous = (A.axis == 0);
+
+  // ---- tile geometry
+  int q0 = 0, stride = 0, x0 = 0, o = 0;
+  long long base = 0;
+  if (contiguous) {
+    q0 = blockIdx.x * P;
+  } else {
+    const int W = 2 * P;
+    const int xt = blockIdx.x % A.tiles_x;
+    o = blockIdx.x / A.tiles_x;
+    x0 = xt * W;
+    if (A.axis == 1) {
+      stride = A.nx;
+      base = x0 + (long long)o * A.nx * A.ny;
+      if (A.ndim == 3 && o == 0) return;  // z = 0 plane: boundary, stays zero
+    } else {
+      stride = A.nx * A.ny;
+      base = x0 + (long long)o * A.nx;
+      if (o == 0) return;                  // y = 0 row: boundary, stays zero
+    }
+  }
+
+  // ---- tile load / store helpers
+  auto load_tile = [&](const T* __restrict__ src, C* buf) {
+    if (contiguous) {
+      for (int idx = tid; idx < P * (N / 2); idx += NT) {
+        const int pp = idx / (N / 2), j2 = idx % (N / 2);
+        const int q = q0 + pp;
+        VT a = {T(0), T(0)}, b = {T(0), T(0)};
+        if (q < A.npairs) {
+          a = reinterpret_cast<const VT*>(src + (size_t)(2 * q) * A.nx)[j2];
+          b = reinterpret_cast<const VT*>(src + (size_t)(2 * q + 1) * A.nx)[j2];
+        }
+        buf[pp * LP + L::at(2 * j2)] = C{a.x, b.x};
+        buf[pp * LP + L::at(2 * j2 + 1)] = C{a.y, b.y};
+      }
+    } else {
+      for (int idx = tid; idx < P * N; idx += NT) {
+        const int j = idx / P, pp = idx % P;
+        const VT v = reinterpret_cast<const VT*>(src + (size_t)base + (size_t)j * stride)[pp];
+        buf[pp * LP + L::at(j)] = C{v.x, v.y};
+      }
+    }
+  };
+  auto store_tile = [&](const C* buf, T* __restrict__ dst) {
+    if (contiguous) {
+      for (int idx = tid; idx < P * (N / 2); idx += NT) {
+        const int pp = idx / (N / 2), j2 = idx % (N / 2);
+        const int q = q0 + pp;
+        if (q < A.npairs) {
+          const C c0 = buf[pp * LP + L::at(2 * j2)], c1 = buf[pp * LP + L::at(2 * j2 + 1)];
+          reinterpret_cast<VT*>(dst + (size_t)(2 * q) * A.nx)[j2] = VT{c0.x, c1.x};
+          reinterpret_cast<VT*>(dst + (size_t)(2 * q + 1) * A.nx)[j2] = VT{c0.y, c1.y};
+        }
+      }
+    } else {
+      for (int idx = tid; idx < P * N; idx += NT) {
+        const int j = idx / P, pp = idx % P;
+        const C c = buf[pp * LP + L::at(j)];
+        reinterpret_cast<VT*>(dst + (size_t)base + (size_t)j * stride)[pp] = VT{c.x, c.y};
+      }
+    }
+  };
+  // dense user layout: rows of nx-1 interior values, only rows with y >= 1 (and z >= 1 in 3D)
+  auto dense_row = [&](int r) -> long long {
+    const int y = r % A.ny, z = r / A.ny;
+    if (y == 0 || (A.ndim == 3 && z == 0)) return -1;
+    const long long dr = (A.ndim == 3 ? (long long)(z - 1) * (A.ny - 1) : 0LL) + (y - 1);
+    return dr * (A.nx - 1);
+  };
+  auto load_dense = [&](const T* __restrict__ src, C* buf) {
+    for (int idx = tid; idx < P * N; idx += NT) {
+      const int pp = idx / N, x = idx % N;
+      const int q = q0 + pp;
+      T a = T(0), b = T(0);
+      if (q < A.npairs && x > 0) {
+        const long long ra = dense_row(2 * q), rb = dense_row(2 * q + 1);
+        if (ra >= 0) a = src[ra + x - 1];
+        if (rb >= 0) b = src[rb + x - 1];
+      }
+      buf[pp * LP + L::at(x)] = C{a, b};
+    }
+  };
+  auto store_dense = [&](const C* buf, T* __restrict__ dst) {
+    for (int idx = tid; idx < P * N; idx += NT) {
+      const int pp = idx / N, x = idx % N;
+      const int q = q0 + pp;
+      if (q < A.npairs && x > 0) {
+        const C c = buf[pp * LP + L::at(x)];
+        const long long ra = dense_row(2 * q), rb = dense_row(2 * q + 1);
+        if (ra >= 0) dst[ra + x - 1] = c.x;
+        if (rb >= 0) dst[rb + x - 1] = c.y;
+      }
+    }
+  };
+
+  // ---- loads
+  if (op == OP_ENTRY || op == OP_PACK) {
+    load_dense(A.in0, b0);
+  } else {
+    load_tile(A.in0, b0);
+    if (two) load_tile(A.in1, b1);
+  }
+  __syncthreads();
+
+  if (op == OP_PACK) {
+    store_tile(b0, A.out0);
+    return;
+  }
+  if (op == OP_UNPACK) {
+    store_dense(b0, A.out0);
+    return;
+  }
+
+  // ---- per-pencil constants of the spectral epilogues (last axis passes only)
+  const int la = A.axis;  // transformed axis
+  T pz[2] = {T(0), T(0)}, pe[2] = {T(1), T(1)}, pc[2] = {T(1), T(1)};
+  const T* zj = A.zeta[la];
+  const T* ej = A.ex[la];
+  const T* cj = A.ec[la];
+  if (op == OP_RK1 || op == OP_S1 || op == OP_S2) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int x = x0 + 2 * p + s;
+      pz[s] = A.zeta[0][x];
+      pe[s] = A.ex[0][x];
+      pc[s] = A.ec[0][x];
+      if (A.ndim == 3) {
+        pz[s] += A.zeta[1][o];
+        pe[s] *= A.ex[1][o];
+        pc[s] *= A.ec[1][o];
+      }
+    }
+  }
+
+  // ---- DST program
+  int nd = 0, bsel[3] = {0, 0, 0}, epi[3] = {EPI_PLAIN, EPI_PLAIN, EPI_PLAIN};
+  switch (op) {
+    case OP_ENTRY: case OP_EXIT: case OP_TRANSFORM: nd = 1; break;
+    case OP_REACT: nd = 2; epi[0] = EPI_REACT; break;
+    case OP_RK1: nd = 3; bsel[1] = 1; epi[1] = EPI_RK1; break;
+    case OP_S1: nd = 3; bsel[1] = 1; epi[1] = EPI_S1; break;
+    case OP_S2: nd = 2; epi[0] = EPI_S2; break;
+    default: break;
+  }
+  C* const b0p = b0 + p * LP;
+  C* const b1p = b1 + p * LP;
+  C* const scrp = scr + p * (TPP > 32 ? TPP / 32 : 1);
+  const T tau = A.tau, c2 = A.c2, flin = A.flin, fcub = A.fcub;
+
+  for (int s = 0; s < nd; ++s) {
+    const int kind = epi[s];
+    C* bp = bsel[s] ? b1p : b0p;
+    dst_pair<T, N>(bp, tw, sn, l, scrp, A.sc, [&](int j, C w) -> C {
+      if (kind == EPI_PLAIN) return w;
+      if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
+      const T zjj = zj[j], ejj = ej[j];
+      T out[2];
+      const T wv[2] = {w.x, w.y};
+      if (kind == EPI_RK1) {
+        const C u = b0p[L::at(j)];
+        const T uv[2] = {u.x, u.y};
+        T nv[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const T zeta = pz[t] + zjj, E = pe[t] * ejj;
+          nv[t] = E * uv[t] + tau * phi1_only(zeta, E) * wv[t];
+        }
+        b0p[L::at(j)] = C{nv[0], nv[1]};
+        return w;
+      }
+      if (kind == EPI_S1) {
+        const T cjj = cj[j];
+        const C u = b0p[L::at(j)];
+        const T uv[2] = {u.x, u.y};
+        T u2[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj;
+          T p1, p2;
+          phi12(zeta, E, p1, p2);
+          const T p1c = phi1_only(c2 * zeta, Ec);
+          u2[t] = Ec * uv[t] + c2 * tau * p1c * wv[t];
+          out[t] = E * uv[t] + tau * (p1 - p2 / c2) * wv[t];
+        }
+        b0p[L::at(j)] = C{u2[0], u2[1]};
+        return C{out[0], out[1]};
+      }
+      // EPI_S2: P from the second buffer
+      const C pp = b1p[L::at(j)];
+      const T pv[2] = {pp.x, pp.y};
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const T zeta = pz[t] + zjj, E = pe[t] * ejj;
+        T p1, p2;
+        phi12(zeta, E, p1, p2);
+        out[t] = pv[t] + (tau / c2) * p2 * wv[t];
+      }
+      return C{out[0], out[1]};
+    });
+    if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
+  }
+
+  if (op == OP_EXIT) store_dense(b0, A.out0);
+  else store_tile(b0, A.out0);
+}
+
+// Host-side description of one instantiation.
+struct KernelInfo {
+  const void* fn;
+  int N;
+  int tpp;
+  int lp;
+  int elem;   // sizeof(T)
+};
+
+template <class T, int N> KernelInfo kernel_info() {
+  using L = PairLayout<T, N>;
+  return KernelInfo{reinterpret_cast<const void*>(&pass_kernel<T, N>), N, L::TPP, L::LP, (int)sizeof(T)};
+}
+
+// shared memory bytes of a launch
+inline size_t pass_smem_bytes(const KernelInfo& k, int P, int nbuf) {
+  const size_t c = 2 * (size_t)k.elem;
+  const size_t bufs = (size_t)nbuf * P * k.lp * c;
+  const size_t scr = (size_t)P * (k.tpp > 32 ? k.tpp / 32 : 1) * c;
+  return bufs + scr;
+}
+
+}  // namespace etd

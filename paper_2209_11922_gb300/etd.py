@@ -1,0 +1,143 @@
+"""Python binding of the C ABI: a plan object over device tensors (PyTorch for memory and streams).
+
+Every step of the solve runs in the library's CUDA kernels; this module only checks shapes and
+dtypes and passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _native as nat
+
+_DT = {"f64": nat.ETD_F64, "f32": nat.ETD_F32}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Plan:
+    """EIFE1/EIFE2 plan for u_t = D Lap u + flin u + fcub u^3 on a rectangle (2D or 3D).
+
+    N: intervals per axis (N_x first); h: mesh sizes (default 1/N, the unit square/cube).
+    Fields are torch tensors of shape (N_z-1, N_y-1, N_x-1) or (N_y-1, N_x-1), x fastest.
+    """
+
+    def __init__(self, N: Sequence[int], D: float, tau: float, scheme: int = 2, dtype: str = "f64",
+                 h: Optional[Sequence[float]] = None, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0):
+        L = nat.lib()
+        self.N = tuple(int(n) for n in N)
+        self.ndim = len(self.N)
+        self.h = tuple(float(x) for x in (h if h is not None else [1.0 / n for n in self.N]))
+        if len(self.h) != self.ndim:
+            raise ValueError("h must have one entry per axis")
+        self.D, self.tau, self.scheme, self.dtype = float(D), float(tau), int(scheme), dtype
+        opt = nat.EtdOptions()
+        L.etd_options_default(ctypes.byref(opt))
+        opt.dtype = _DT[dtype]
+        opt.c2, opt.flin, opt.fcub = float(c2), float(flin), float(fcub)
+        Na = (ctypes.c_int64 * 3)(*(list(self.N) + [1] * (3 - self.ndim)))
+        ha = (ctypes.c_double * 3)(*(list(self.h) + [1.0] * (3 - self.ndim)))
+        handle = ctypes.c_void_p()
+        nat.check(L.etd_plan_create(ctypes.byref(handle), self.ndim, Na, ha, self.D, self.tau, self.scheme,
+                                    ctypes.byref(opt)), "etd_plan_create")
+        self._h = handle
+
+    # ------------------------------------------------------------------ helpers
+    @property
+    def shape(self) -> tuple:
+        return tuple(n - 1 for n in reversed(self.N))
+
+    @property
+    def torch_dtype(self):
+        torch = _torch()
+        return torch.float32 if self.dtype == "f32" else torch.float64
+
+    @property
+    def np_dtype(self):
+        return np.float32 if self.dtype == "f32" else np.float64
+
+    def _check_field(self, u, name="u"):
+        torch = _torch()
+        if not isinstance(u, torch.Tensor) or not u.is_cuda:
+            raise TypeError(f"{name} must be a CUDA torch.Tensor")
+        if u.dtype != self.torch_dtype or tuple(u.shape) != self.shape or not u.is_contiguous():
+            raise ValueError(f"{name} must be contiguous {self.torch_dtype} of shape {self.shape}")
+        return ctypes.c_void_p(u.data_ptr())
+
+    # ------------------------------------------------------------------ API
+    def run(self, u, nsteps: int, stream=None):
+        nat.check(nat.lib().etd_run(self._h, self._check_field(u), int(nsteps), _stream_ptr(stream)), "etd_run")
+        return u
+
+    def step(self, u, stream=None):
+        nat.check(nat.lib().etd_step(self._h, self._check_field(u), _stream_ptr(stream)), "etd_step")
+        return u
+
+    def run_host(self, u_host: np.ndarray, nsteps: int, stream=None) -> np.ndarray:
+        """Host array in, host array out (copies in/out happen inside the library call)."""
+        if not (isinstance(u_host, np.ndarray) and u_host.dtype == self.np_dtype and u_host.shape == self.shape
+                and u_host.flags["C_CONTIGUOUS"]):
+            raise ValueError(f"u_host must be a C-contiguous {self.np_dtype} array of shape {self.shape}")
+        nat.check(nat.lib().etd_run_host(self._h, u_host.ctypes.data_as(ctypes.c_void_p), int(nsteps),
+                                         _stream_ptr(stream)), "etd_run_host")
+        return u_host
+
+    def apply_dst(self, axis: int, inp, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(inp)
+        nat.check(nat.lib().etd_apply_dst(self._h, int(axis), self._check_field(inp, "in"),
+                                          self._check_field(out, "out"), _stream_ptr(stream)), "etd_apply_dst")
+        return out
+
+    def monitor(self, u, stream=None) -> dict:
+        m = nat.EtdMonitors()
+        st = nat.lib().etd_monitor(self._h, self._check_field(u), ctypes.byref(m), _stream_ptr(stream))
+        if st not in (nat.ETD_OK, nat.ETD_ERR_NONFINITE):
+            nat.check(st, "etd_monitor")
+        return {"mass": m.mass, "energy": m.energy, "maxabs": m.maxabs, "nonfinite": int(m.nonfinite),
+                "status": st}
+
+    def run_profiled(self, u, nsteps: int, stream=None) -> dict:
+        ms = (ctypes.c_double * nat.ETD_NUM_PASS_KINDS)()
+        cnt = (ctypes.c_int64 * nat.ETD_NUM_PASS_KINDS)()
+        nat.check(nat.lib().etd_run_profiled(self._h, self._check_field(u), int(nsteps), _stream_ptr(stream), ms, cnt),
+                  "etd_run_profiled")
+        L = nat.lib()
+        return {L.etd_pass_kind_name(k).decode(): (ms[k], int(cnt[k])) for k in range(nat.ETD_NUM_PASS_KINDS)}
+
+    def info(self) -> dict:
+        i = nat.EtdPlanInfo()
+        nat.check(nat.lib().etd_get_plan_info(self._h, ctypes.byref(i)), "etd_get_plan_info")
+        return {"ndim": i.ndim, "N": tuple(i.N[:i.ndim]), "unknowns": i.unknowns,
+                "workspace_bytes": i.workspace_bytes, "kernels_per_step": i.kernels_per_step,
+                "bytes_per_step": i.bytes_per_step, "dtype": i.dtype, "scheme": i.scheme}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().etd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,210 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Tolerances (relative to the oracle's norms): FP64 rel L2 and rel Linf <= 1e-12; FP32 <= 1e-5 (the
+FP32 input is rounded first and the oracle runs on the rounded values in FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import etd as oetd
+from oracle import monitors as omon
+from oracle import transforms as otr
+from paper_2209_11922_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def _plan(N, D, tau, scheme=2, dtype="f64", **kw):
+    from paper_2209_11922_gb300.etd import Plan
+    return Plan(N, D, tau, scheme=scheme, dtype=dtype, **kw)
+
+
+def _to_dev(a, dtype):
+    t = torch.from_numpy(np.ascontiguousarray(a.astype(np.float32 if dtype == "f32" else np.float64)))
+    return t.cuda()
+
+
+def _rel(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    l2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    linf = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    return l2, linf
+
+
+def _check(got, ref, dtype, what=""):
+    l2, linf = _rel(got, ref)
+    assert l2 <= TOL[dtype] and linf <= TOL[dtype], f"{what}: rel L2 {l2:.3e} rel Linf {linf:.3e}"
+
+
+# ------------------------------------------------------------------ single-axis DST-I kernels
+DST_CASES = [
+    ((4, 6), "f64"), ((8, 12), "f32"), ((16, 24), "f64"), ((32, 48), "f32"), ((64, 96), "f64"),
+    ((128, 192), "f32"), ((256, 384), "f64"), ((512, 4), "f32"), ((1024, 6), "f64"),
+    ((2048, 4), "f32"), ((768, 4), "f64"), ((1536, 4), "f32"), ((6, 2048), "f64"), ((4, 1536), "f64"),
+    ((4, 768), "f32"), ((12, 8, 6), "f64"), ((16, 6, 96), "f32"), ((4, 1024, 4), "f32"),
+]
+
+
+@pytest.mark.parametrize("N,dtype", DST_CASES, ids=lambda v: str(v))
+def test_dst_axis_matches_definition(N, dtype):
+    shape = tuple(n - 1 for n in reversed(N))
+    U = inputs.uniform_field(shape, -1, 1, seed=sum(N))
+    if dtype == "f32":
+        U = U.astype(np.float32).astype(np.float64)
+    with _plan(N, 0.1, 0.01, dtype=dtype) as pl:
+        d = _to_dev(U, dtype)
+        for axis in range(len(N)):
+            got = pl.apply_dst(axis, d).cpu().numpy()
+            ref = otr.dst_axis(U, axis)
+            tol = 1e-13 if dtype == "f64" else 2e-6
+            l2, linf = _rel(got, ref)
+            assert l2 <= tol and linf <= 5 * tol, (axis, l2, linf)
+
+
+# ------------------------------------------------------------------ full steps
+STEP_CASES = [
+    # N, D, tau, nsteps, scheme, dtype, u range
+    ((64, 64), 1e-2, 1e-2, 100, 2, "f64", 0.9),      # the 64x64 Allen-Cahn workload, full run
+    ((64, 64), 1e-2, 1e-2, 100, 2, "f32", 0.9),
+    ((64, 64), 1e-2, 1e-2, 100, 1, "f64", 0.9),
+    ((96, 64), 3e-3, 2e-2, 20, 2, "f64", 0.9),       # several tiles per axis, non-power-of-two
+    ((48, 192), 1e-3, 1e-2, 10, 1, "f32", 0.9),
+    ((6, 4), 0.05, 0.1, 7, 2, "f64", 0.9),           # smallest supported grids
+    ((4, 4), 0.05, 0.1, 3, 1, "f64", 0.9),
+    ((384, 128), 1e-4, 5e-3, 5, 2, "f32", 0.05),
+    ((32, 48, 64), 1e-3, 1e-2, 6, 2, "f64", 0.9),    # 3D
+    ((32, 48, 64), 1e-3, 1e-2, 6, 2, "f32", 0.9),
+    ((24, 16, 12), 1e-2, 5e-2, 4, 1, "f64", 0.9),
+    ((4, 6, 8), 0.1, 0.1, 3, 2, "f64", 0.9),
+    ((64, 64, 64), 1e-3, 1e-2, 5, 2, "f32", 0.9),
+]
+
+
+@pytest.mark.parametrize("case", STEP_CASES, ids=lambda c: f"{c[0]}-rk{c[4]}-{c[5]}-n{c[3]}")
+def test_steps_match_oracle(case):
+    N, D, tau, nsteps, scheme, dtype, amp = case
+    shape = tuple(n - 1 for n in reversed(N))
+    U0 = inputs.uniform_field(shape, -amp, amp, seed=101 + len(N) + N[0])
+    if dtype == "f32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    h = tuple(1.0 / n for n in N)
+    ref = oetd.run(U0, N, h, D, tau, nsteps, scheme)
+    with _plan(N, D, tau, scheme=scheme, dtype=dtype) as pl:
+        d = _to_dev(U0, dtype)
+        pl.run(d, nsteps)
+        torch.cuda.synchronize()
+        _check(d.cpu().numpy(), ref, dtype, str(case))
+
+
+def test_nonunit_mesh_and_reaction_options():
+    N, h, D, tau = (32, 24), (0.05, 0.02), 0.02, 0.03
+    U0 = inputs.uniform_field((23, 31), -1, 1, seed=5)
+    ref = oetd.run(U0, N, h, D, tau, 5, 2, c2=0.75, flin=2.0, fcub=-0.5)
+    with _plan(N, D, tau, 2, "f64", h=h, c2=0.75, flin=2.0, fcub=-0.5) as pl:
+        d = _to_dev(U0, "f64")
+        pl.run(d, 5)
+        _check(d.cpu().numpy(), ref, "f64")
+
+
+def test_split_runs_match_one_run_to_rounding():
+    N, D, tau = (64, 96), 1e-3, 1e-2
+    U0 = inputs.uniform_field((95, 63), -0.9, 0.9, seed=9)
+    with _plan(N, D, tau) as pl:
+        a, b = _to_dev(U0, "f64"), _to_dev(U0, "f64")
+        pl.run(a, 40)
+        pl.run(b, 15)
+        pl.run(b, 25)
+        _check(b.cpu().numpy(), a.cpu().numpy(), "f64")
+        c = _to_dev(U0, "f64")
+        pl.run(c, 0)
+        assert torch.equal(c, _to_dev(U0, "f64"))
+
+
+def test_graph_replay_matches_direct_launches(monkeypatch):
+    N, D, tau = (128, 64), 1e-3, 1e-2
+    U0 = inputs.uniform_field((63, 127), -0.9, 0.9, seed=12)
+    with _plan(N, D, tau, dtype="f32") as pl:
+        a = _to_dev(U0, "f32")
+        pl.run(a, 70)            # two graph replays of 32 steps and 6 direct steps
+        b = _to_dev(U0, "f32")
+        for _ in range(70):
+            pl.step(b)           # direct launches only, one entry/exit per step
+        _check(b.cpu().numpy().astype(np.float64), a.cpu().numpy().astype(np.float64), "f32")
+
+
+def test_run_host_equals_device_run():
+    N, D, tau = (64, 48), 1e-3, 1e-2
+    U0 = inputs.uniform_field((47, 63), -0.9, 0.9, seed=13)
+    with _plan(N, D, tau, dtype="f32") as pl:
+        d = _to_dev(U0, "f32")
+        pl.run(d, 33)
+        hbuf = U0.astype(np.float32)
+        pl.run_host(hbuf, 33)
+        np.testing.assert_array_equal(hbuf, d.cpu().numpy())
+
+
+@pytest.mark.parametrize("N,dtype", [((64, 48), "f64"), ((32, 24, 16), "f32")])
+def test_monitors_match_oracle(N, dtype):
+    shape = tuple(n - 1 for n in reversed(N))
+    U = inputs.uniform_field(shape, -1.2, 1.2, seed=21)
+    if dtype == "f32":
+        U = U.astype(np.float32).astype(np.float64)
+    h = tuple(1.0 / n for n in N)
+    D = 0.07
+    ref = omon.monitors(U, N, h, D)
+    with _plan(N, D, 0.01, dtype=dtype) as pl:
+        m = pl.monitor(_to_dev(U, dtype))
+    for k in ("mass", "energy", "maxabs"):
+        assert m[k] == pytest.approx(ref[k], rel=1e-12), k
+    assert m["nonfinite"] == 0 and m["status"] == 0
+
+
+def test_monitor_flags_nonfinite_values():
+    from paper_2209_11922_gb300 import _native as nat
+    U = inputs.uniform_field((15, 15), -1, 1, seed=4)
+    U[3, 7] = np.nan
+    U[0, 0] = np.inf
+    with _plan((16, 16), 0.1, 0.01) as pl:
+        m = pl.monitor(_to_dev(U, "f64"))
+    assert m["status"] == nat.ETD_ERR_NONFINITE and m["nonfinite"] == 2
+
+
+# ------------------------------------------------------------------ full-size workloads
+def _full_size(w, dtype, nsteps, scheme=2):
+    U0 = w.u0()
+    if dtype == "f32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    ref = oetd.run(U0, w.N, w.h, w.D, w.tau, nsteps, scheme)
+    with _plan(w.N, w.D, w.tau, scheme=scheme, dtype=dtype) as pl:
+        d = _to_dev(U0, dtype)
+        pl.run(d, nsteps)
+        _check(d.cpu().numpy(), ref, dtype, f"{w.name} {dtype}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_full_size_2d_1024_first_steps(dtype, scheme):
+    _full_size(inputs.AC2D_1024, dtype, 3, scheme)
+
+
+def test_full_size_3d_256_first_step():
+    _full_size(inputs.AC3D_256, "f32", 1)
+
+
+def test_full_size_sine_mode_decays_exactly():
+    """f = 0 at 1024^2: a product sine mode is an eigenvector of every pass; the run must give
+    exp(-n tau D (mu_p + mu_q)) times the mode (closed form of Section 4)."""
+    N, D, tau, n = (1024, 1024), 1e-4, 5e-3, 64
+    x = np.arange(1, 1024) / 1024
+    p, q = 37, 250
+    U0 = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x))
+    mu = lambda k: 6 * 1024 ** 2 * (1 - np.cos(k * np.pi / 1024)) / (2 + np.cos(k * np.pi / 1024))
+    ref = np.exp(-n * tau * D * (mu(p) + mu(q))) * U0
+    for dtype in ("f64", "f32"):
+        with _plan(N, D, tau, 2, dtype, flin=0.0, fcub=0.0) as pl:
+            d = _to_dev(U0, dtype)
+            pl.run(d, n)
+            _check(d.cpu().numpy(), ref, dtype, dtype)

@@ -1,0 +1,75 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports every function that
+include/etd.h declares, and rejects invalid arguments before touching the device."""
+import ctypes
+
+import pytest
+
+from paper_2209_11922_gb300 import _native as nat
+
+
+@pytest.fixture(scope="module")
+def L():
+    try:
+        return nat.lib()
+    except RuntimeError as e:  # the library is built by __graft_entry__.build()
+        pytest.fail(str(e))
+
+
+def test_library_exports_every_declared_function(L):
+    names = nat.header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(nat._SIGS) <= set(names)
+
+
+def _create(L, ndim, N, h, D=0.1, tau=0.01, scheme=2, opt=None):
+    Na = (ctypes.c_int64 * 3)(*N)
+    ha = (ctypes.c_double * 3)(*h)
+    p = ctypes.c_void_p()
+    return L.etd_plan_create(ctypes.byref(p), ndim, Na, ha, D, tau, scheme, opt), p
+
+
+@pytest.mark.parametrize("case", [
+    dict(ndim=1), dict(ndim=4), dict(N=(1, 8, 1)), dict(N=(7, 8, 1)), dict(h=(0.0, 0.1, 1)),
+    dict(h=(-1.0, 0.1, 1)), dict(D=0.0), dict(D=float("nan")), dict(tau=-1.0), dict(scheme=3),
+    dict(tau=float("inf")),
+])
+def test_invalid_arguments_are_rejected_on_the_host(L, case):
+    args = dict(ndim=2, N=(8, 8, 1), h=(0.125, 0.125, 1.0), D=0.1, tau=0.01, scheme=2)
+    args.update(case)
+    st, p = _create(L, args["ndim"], args["N"], args["h"], args["D"], args["tau"], args["scheme"])
+    assert st == nat.ETD_ERR_INVALID_ARG and not p.value
+    assert L.etd_last_error()  # a detail string is set
+
+
+@pytest.mark.parametrize("c2", [0.0, 1.5, float("nan")])
+def test_invalid_c2_rejected(L, c2):
+    opt = nat.EtdOptions()
+    L.etd_options_default(ctypes.byref(opt))
+    opt.c2 = c2
+    st, _ = _create(L, 2, (8, 8, 1), (0.125, 0.125, 1.0), opt=ctypes.byref(opt))
+    assert st == nat.ETD_ERR_INVALID_ARG
+
+
+def test_unsupported_axis_length(L):
+    st, _ = _create(L, 2, (10, 8, 1), (0.1, 0.125, 1.0))
+    assert st == nat.ETD_ERR_UNSUPPORTED
+    st, _ = _create(L, 3, (8, 8, 4096), (0.1, 0.125, 1.0))
+    assert st == nat.ETD_ERR_UNSUPPORTED
+
+
+def test_null_arguments(L):
+    assert L.etd_run(None, None, 1, None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_monitor(None, None, None, None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_destroy(None) == nat.ETD_OK
+    assert L.etd_options_default(None) == nat.ETD_ERR_INVALID_ARG
+
+
+def test_defaults_and_names(L):
+    opt = nat.EtdOptions()
+    assert L.etd_options_default(ctypes.byref(opt)) == nat.ETD_OK
+    assert (opt.dtype, opt.c2, opt.flin, opt.fcub) == (nat.ETD_F64, 0.5, 1.0, -1.0)
+    assert L.etd_status_string(nat.ETD_ERR_NONFINITE) == b"non-finite values"
+    assert [L.etd_pass_kind_name(k) for k in range(nat.ETD_NUM_PASS_KINDS)][1] == b"x_react"
+    assert L.etd_pass_kind_name(99) is None

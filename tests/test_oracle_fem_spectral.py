@@ -137,3 +137,31 @@ def test_mode_rates_sum_per_axis():
     H = spectral.mode_rates(mus, 0.5)
     assert H.shape == (2, 3)  # storage order (y, x)
     np.testing.assert_allclose(H, 0.5 * (np.array([[10.0], [20.0]]) + np.array([[1.0, 2.0, 3.0]])))
+
+
+@pytest.mark.parametrize("N", [4, 6, 33, 96])
+def test_sine_matrix_is_the_numerical_eigenbasis(N):
+    """oracle.transforms.sine_matrix diagonalises the assembled A and B and is an involution."""
+    from oracle import transforms
+    S = transforms.sine_matrix(N)
+    A, B = fem.assemble_1d(N, 1.0 / N)
+    for M in (A, B):
+        D = S @ M @ S
+        assert np.abs(D - np.diag(np.diag(D))).max() < 1e-12 * np.abs(M).max()
+    np.testing.assert_allclose(S @ S, np.eye(N - 1), atol=1e-13)
+
+
+@pytest.mark.parametrize("N,h", [((6, 5), (1 / 6, 0.2)), ((4, 5, 3), (0.25, 0.2, 1 / 3))])
+def test_monitors_match_global_assembly(N, h):
+    """mass = 1^T M U and the quadratic energy term 1/2 U^T K U against the globally assembled M, K."""
+    from oracle import monitors
+    from paper_2209_11922_gb300.inputs import uniform_field
+    D = 0.3
+    U = uniform_field(tuple(n - 1 for n in reversed(N)), -1, 1, seed=2)
+    M, K = fem.assemble_global(N, h, D)
+    u = U.ravel()
+    m = monitors.monitors(U, N, h, D)
+    assert m["mass"] == pytest.approx(float(np.ones_like(u) @ (M @ u)), rel=1e-13)
+    pot = np.prod(h) * 0.25 * np.sum((u * u - 1) ** 2)
+    assert m["energy"] == pytest.approx(0.5 * float(u @ (K @ u)) + pot, rel=1e-13)
+    assert m["maxabs"] == pytest.approx(np.abs(u).max()) and m["nonfinite"] == 0
