@@ -13,8 +13,11 @@ from .etd import mode_product
 
 
 def sine_matrix(N: int) -> np.ndarray:
+    """sqrt(2/N) sin(pi i j / N); i j is reduced modulo 2N first (exact integer arithmetic, the
+    sine has period 2N in i j), so the angle stays below 2 pi and carries no large rounding error."""
     i = np.arange(1, N)
-    return np.sqrt(2.0 / N) * np.sin(np.outer(i, i) * np.pi / N)
+    ij = np.outer(i, i) % (2 * N)
+    return np.sqrt(2.0 / N) * np.sin(ij * np.pi / N)
 
 
 def dst_axis(U: np.ndarray, axis: int) -> np.ndarray:

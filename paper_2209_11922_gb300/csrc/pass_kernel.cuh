@@ -84,6 +84,17 @@ template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E) {
   return (T(1) - E) / zeta;
 }
 
+// Asynchronous global -> shared copies (cp.async): every load of a tile is in flight at once and
+// the CTA waits a single time, instead of one memory latency per register-staged loop iteration.
+template <int B> __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
@@ -130,24 +141,24 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> A) {
   }
 
   // ---- tile load / store helpers
+  // issues cp.async copies of one field's tile into buf (complete after cp_async_wait_all)
   auto load_tile = [&](const T* __restrict__ src, C* buf) {
     if (contiguous) {
-      for (int idx = tid; idx < P * (N / 2); idx += NT) {
-        const int pp = idx / (N / 2), j2 = idx % (N / 2);
+      for (int idx = tid; idx < P * N; idx += NT) {
+        const int pp = idx / N, j = idx % N;
         const int q = q0 + pp;
-        VT a = {T(0), T(0)}, b = {T(0), T(0)};
+        C* d = &buf[pp * LP + L::at(j)];
         if (q < A.npairs) {
-          a = reinterpret_cast<const VT*>(src + (size_t)(2 * q) * A.nx)[j2];
-          b = reinterpret_cast<const VT*>(src + (size_t)(2 * q + 1) * A.nx)[j2];
+          cp_async<sizeof(T)>(&d->x, src + (size_t)(2 * q) * A.nx + j);
+          cp_async<sizeof(T)>(&d->y, src + (size_t)(2 * q + 1) * A.nx + j);
+        } else {
+          *d = C{T(0), T(0)};
         }
-        buf[pp * LP + L::at(2 * j2)] = C{a.x, b.x};
-        buf[pp * LP + L::at(2 * j2 + 1)] = C{a.y, b.y};
       }
     } else {
       for (int idx = tid; idx < P * N; idx += NT) {
         const int j = idx / P, pp = idx % P;
-        const VT v = reinterpret_cast<const VT*>(src + (size_t)base + (size_t)j * stride)[pp];
-        buf[pp * LP + L::at(j)] = C{v.x, v.y};
+        cp_async<2 * sizeof(T)>(&buf[pp * LP + L::at(j)], src + (size_t)base + (size_t)j * stride + 2 * pp);
       }
     }
   };
@@ -209,6 +220,7 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> A) {
   } else {
     load_tile(A.in0, b0);
     if (two) load_tile(A.in1, b1);
+    cp_async_wait_all();
   }
   __syncthreads();
 

@@ -40,6 +40,13 @@ def _check(got, ref, dtype, what=""):
 
 
 # ------------------------------------------------------------------ single-axis DST-I kernels
+def _dst_tol(N, dtype):
+    """The odd outputs of the DST are prefix sums of N/2 FFT outputs, so rounding errors grow like
+    sqrt(N/2) eps (random walk); allow 4x that (rel L2), 12x for Linf."""
+    eps = 2.0 ** -24 if dtype == "f32" else 2.0 ** -53
+    return 4.0 * np.sqrt(max(N, 8) / 2.0) * eps
+
+
 DST_CASES = [
     ((4, 6), "f64"), ((8, 12), "f32"), ((16, 24), "f64"), ((32, 48), "f32"), ((64, 96), "f64"),
     ((128, 192), "f32"), ((256, 384), "f64"), ((512, 4), "f32"), ((1024, 6), "f64"),
@@ -59,9 +66,9 @@ def test_dst_axis_matches_definition(N, dtype):
         for axis in range(len(N)):
             got = pl.apply_dst(axis, d).cpu().numpy()
             ref = otr.dst_axis(U, axis)
-            tol = 1e-13 if dtype == "f64" else 2e-6
             l2, linf = _rel(got, ref)
-            assert l2 <= tol and linf <= 5 * tol, (axis, l2, linf)
+            tol = _dst_tol(N[axis], dtype)
+            assert l2 <= tol and linf <= 3 * tol, (axis, l2, linf, tol)
 
 
 # ------------------------------------------------------------------ full steps
@@ -190,6 +197,12 @@ def test_full_size_2d_1024_first_steps(dtype, scheme):
     _full_size(inputs.AC2D_1024, dtype, 3, scheme)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_full_size_2d_1024_first_100_steps(dtype):
+    """The first 100 ETDRK2 steps of the 1024^2 workload (T = 0.5) stay within the tolerance."""
+    _full_size(inputs.AC2D_1024, dtype, 100, 2)
+
+
 def test_full_size_3d_256_first_step():
     _full_size(inputs.AC3D_256, "f32", 1)
 
@@ -199,7 +212,7 @@ def test_full_size_sine_mode_decays_exactly():
     exp(-n tau D (mu_p + mu_q)) times the mode (closed form of Section 4)."""
     N, D, tau, n = (1024, 1024), 1e-4, 5e-3, 64
     x = np.arange(1, 1024) / 1024
-    p, q = 37, 250
+    p, q = 5, 40          # total decay exp(-0.5): transform rounding in other modes stays below tolerance
     U0 = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x))
     mu = lambda k: 6 * 1024 ** 2 * (1 - np.cos(k * np.pi / 1024)) / (2 + np.cos(k * np.pi / 1024))
     ref = np.exp(-n * tau * D * (mu(p) + mu(q))) * U0
