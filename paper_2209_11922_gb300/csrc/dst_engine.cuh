@@ -5,15 +5,22 @@
 // i.e. S = sqrt(2/N) P with the sine matrix P of Section 4 (S is symmetric and S^2 = I, so the
 // same routine is the forward transform and its inverse; Section 4 states the DST/iDST per axis).
 //
-// Algorithm (two real pencils a, b packed as one complex sequence c_j = a_j + i b_j):
+// Two real pencils a, b are packed as one complex sequence c_j = a_j + i b_j and transformed by
+// one complex FFT computed with Stockham passes whose butterflies (radix R <= 16 here) run in
+// registers, with one shared-memory exchange per pass. Two variants:
+//
+// ODD (used for FP32): the odd extension z_j = c_j, z_{2N-j} = -c_j, z_0 = z_N = 0 of length
+//   M = 2N has DFT Z_k = 2i sum_j c_j sin(pi j k / N) (kernel exp(+2 pi i j k / M)), so the outputs
+//   are -i sc Z_k for k = 1..N-1 (sc = sqrt(2/N)/2). Rounding grows like log N only.
+// RECURRENCE (used for FP64, half the FFT length, M = N):
 //   1. y_j = sin(pi j/N)(c_j + c_{N-j}) + (c_j - c_{N-j})/2 for j = 1..N-1, y_0 = 0.
-//   2. Z = length-N complex DFT of y with kernel exp(+2 pi i j k / N), computed by Stockham passes
-//      whose butterflies (radix R <= 32) run in registers; one shared-memory exchange per pass.
+//   2. Z = length-N DFT of y.
 //   3. With Y^a, Y^b the real DFTs separated from Z: F_{2k} = Im Y_k and
 //      F_{2k+1} = F_{2k-1} + Re Y_k (F_1 = Re Y_0 / 2), i.e. even outputs are
 //      (-i/2)(Z_k - Z_{N-k}) and odd outputs are half a prefix sum of G_0 = Z_0,
 //      G_m = Z_m + Z_{N-m}; the prefix sum runs per thread then across lanes by warp shuffles.
-// The identities in step 1 and 3 follow from splitting y into its even and odd parts about N/2.
+//   The identities follow from splitting y into its even and odd parts about N/2. The prefix sum
+//   lets rounding grow like sqrt(N/2) eps, which FP64 absorbs and FP32 does not.
 //
 // Layout: one pair occupies LP complex slots of shared memory; position j lives at
 // j + j / PADG (one padding slot every PADG entries) so that the strided writes of the first pass
@@ -135,79 +142,88 @@ __device__ __forceinline__ void Dft<T, R>::run(Cx<T>* x) {
   }
 }
 
-// Per-(type, N) pass plan: radices of the Stockham passes and threads per pair (TPP).
-// A thread holds at most 32 (FP32) / 16 (FP64) complex values in a pass.
+// Per-(type, N) pass plan: FFT length M, radices of the Stockham passes, threads per pair (TPP).
+// A thread holds at most 32 (FP32) / 16 (FP64) complex values in a pass; the last radix of an ODD
+// plan is even so that the outputs k < N are exactly the butterfly outputs r < R/2.
 template <int... Rs> struct Radices {};
 template <class T, int N> struct FftPlan;
-#define ETD_PLAN(TYPE, NN, TPP_, ...)                      \
+#define ETD_PLAN(TYPE, NN, ODD_, TPP_, ...)                \
   template <> struct FftPlan<TYPE, NN> {                   \
+    static constexpr bool ODD = ODD_;                      \
+    static constexpr int M = ODD_ ? 2 * NN : NN;           \
     static constexpr int TPP = TPP_;                       \
     using R = Radices<__VA_ARGS__>;                        \
   };
-// powers of two
-ETD_PLAN(float, 4, 1, 4)
-ETD_PLAN(float, 8, 2, 4, 2)
-ETD_PLAN(float, 16, 4, 4, 4)
-ETD_PLAN(float, 32, 4, 8, 4)
-ETD_PLAN(float, 64, 8, 8, 8)
-ETD_PLAN(float, 128, 8, 16, 8)
-ETD_PLAN(float, 256, 16, 16, 16)
-ETD_PLAN(float, 512, 16, 32, 16)
-ETD_PLAN(float, 1024, 32, 32, 32)
-ETD_PLAN(float, 2048, 64, 16, 8, 16)
-ETD_PLAN(double, 4, 1, 4)
-ETD_PLAN(double, 8, 2, 4, 2)
-ETD_PLAN(double, 16, 4, 4, 4)
-ETD_PLAN(double, 32, 4, 8, 4)
-ETD_PLAN(double, 64, 8, 8, 8)
-ETD_PLAN(double, 128, 8, 16, 8)
-ETD_PLAN(double, 256, 16, 16, 16)
-ETD_PLAN(double, 512, 32, 8, 8, 8)
-ETD_PLAN(double, 1024, 64, 16, 8, 8)
-ETD_PLAN(double, 2048, 128, 16, 16, 8)
-// three times a power of two
-ETD_PLAN(float, 6, 1, 6)
-ETD_PLAN(float, 12, 2, 4, 3)
-ETD_PLAN(float, 24, 4, 8, 3)
-ETD_PLAN(float, 48, 4, 12, 4)
-ETD_PLAN(float, 96, 8, 12, 8)
-ETD_PLAN(float, 192, 16, 12, 16)
-ETD_PLAN(float, 384, 32, 12, 32)
-ETD_PLAN(float, 768, 32, 24, 32)
-ETD_PLAN(float, 1536, 64, 16, 3, 32)
-ETD_PLAN(double, 6, 1, 6)
-ETD_PLAN(double, 12, 2, 4, 3)
-ETD_PLAN(double, 24, 4, 8, 3)
-ETD_PLAN(double, 48, 4, 12, 4)
-ETD_PLAN(double, 96, 8, 12, 8)
-ETD_PLAN(double, 192, 16, 12, 16)
-ETD_PLAN(double, 384, 32, 8, 3, 16)
-ETD_PLAN(double, 768, 64, 16, 3, 16)
-ETD_PLAN(double, 1536, 128, 16, 6, 16)
+// FP32: odd extension, M = 2N
+ETD_PLAN(float, 4, true, 2, 4, 2)
+ETD_PLAN(float, 8, true, 4, 4, 4)
+ETD_PLAN(float, 16, true, 8, 8, 4)
+ETD_PLAN(float, 32, true, 8, 8, 8)
+ETD_PLAN(float, 64, true, 16, 16, 8)
+ETD_PLAN(float, 128, true, 16, 16, 16)
+ETD_PLAN(float, 256, true, 64, 8, 8, 8)
+ETD_PLAN(float, 512, true, 128, 16, 8, 8)
+ETD_PLAN(float, 1024, true, 128, 16, 8, 16)
+ETD_PLAN(float, 2048, true, 256, 16, 16, 16)
+ETD_PLAN(float, 6, true, 4, 3, 4)
+ETD_PLAN(float, 12, true, 8, 3, 8)
+ETD_PLAN(float, 24, true, 4, 12, 4)
+ETD_PLAN(float, 48, true, 8, 12, 8)
+ETD_PLAN(float, 96, true, 16, 12, 16)
+ETD_PLAN(float, 192, true, 64, 6, 4, 16)
+ETD_PLAN(float, 384, true, 64, 12, 4, 16)
+ETD_PLAN(float, 768, true, 128, 12, 8, 16)
+ETD_PLAN(float, 1536, true, 256, 12, 16, 16)
+// FP64: recurrence, M = N
+ETD_PLAN(double, 4, false, 1, 4)
+ETD_PLAN(double, 8, false, 2, 4, 2)
+ETD_PLAN(double, 16, false, 4, 4, 4)
+ETD_PLAN(double, 32, false, 4, 8, 4)
+ETD_PLAN(double, 64, false, 8, 8, 8)
+ETD_PLAN(double, 128, false, 8, 16, 8)
+ETD_PLAN(double, 256, false, 16, 16, 16)
+ETD_PLAN(double, 512, false, 32, 8, 8, 8)
+ETD_PLAN(double, 1024, false, 64, 16, 8, 8)
+ETD_PLAN(double, 2048, false, 128, 16, 16, 8)
+ETD_PLAN(double, 6, false, 1, 6)
+ETD_PLAN(double, 12, false, 2, 4, 3)
+ETD_PLAN(double, 24, false, 4, 8, 3)
+ETD_PLAN(double, 48, false, 4, 12, 4)
+ETD_PLAN(double, 96, false, 8, 12, 8)
+ETD_PLAN(double, 192, false, 16, 12, 16)
+ETD_PLAN(double, 384, false, 32, 8, 3, 16)
+ETD_PLAN(double, 768, false, 64, 16, 3, 16)
+ETD_PLAN(double, 1536, false, 128, 16, 6, 16)
 #undef ETD_PLAN
 
 template <class L> struct FirstRadix;
 template <int R0, int... Rs> struct FirstRadix<Radices<R0, Rs...>> { static constexpr int value = R0; };
 
 template <class T, int N> struct PairLayout {
-  static constexpr int TPP = FftPlan<T, N>::TPP;
-  static constexpr int PADG = FirstRadix<typename FftPlan<T, N>::R>::value;
-  static constexpr int LP = N + N / PADG + 1;  // complex slots per pair
+  using Plan = FftPlan<T, N>;
+  static constexpr bool ODD = Plan::ODD;
+  static constexpr int M = Plan::M;
+  static constexpr int TPP = Plan::TPP;
+  static constexpr int PADG = FirstRadix<typename Plan::R>::value;
+  static constexpr int LP = M + M / PADG + 1;  // complex slots per pair
   static __device__ __forceinline__ int at(int j) { return j + j / PADG; }
 };
 
 // ---------------------------------------------------------------------------------------------
-// Stockham passes. Pass with radix R after Ns points are already combined: butterfly jj reads
-// positions jj + r*N/R, twiddles by w_N^{(jj mod Ns) r N/(Ns R)}, and writes
+// Stockham passes over the length-M sequence. Pass with radix R after Ns points are combined:
+// butterfly jj reads positions jj + r*M/R, twiddles by w_M^{(jj mod Ns) r M/(Ns R)}, and writes
 // (jj/Ns)*Ns*R + (jj mod Ns) + r*Ns. In place: all reads, barrier, all writes, barrier.
-// The first pass folds in step 1 (pre-processing of the DST).
+// The first pass folds in the input map of the variant (odd extension or the y_j of the
+// recurrence); the last pass of the ODD variant writes only k < N, already scaled by -i sc.
 template <class T, int N, int NS, bool FIRST, int R, int... Rest>
 __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
-                                         const T* __restrict__ sn, int l) {
+                                         const T* __restrict__ sn, int l, T sc) {
   using L = PairLayout<T, N>;
+  constexpr int M = L::M;
   constexpr int TPP = L::TPP;
-  constexpr int TP = N / R;
+  constexpr int TP = M / R;
   constexpr int QN = (TP + TPP - 1) / TPP;
+  constexpr bool LAST = sizeof...(Rest) == 0;
   Cx<T> v[QN][R];
 #pragma unroll
   for (int q = 0; q < QN; ++q) {
@@ -217,8 +233,17 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
       for (int r = 0; r < R; ++r) {
         const int idx = jj + r * TP;
         Cx<T> xv;
-        if (FIRST) {
-          if (r == 0 && jj == 0) {
+        if constexpr (FIRST && L::ODD) {
+          if (idx == 0 || idx == N) {
+            xv = {T(0), T(0)};
+          } else if (idx < N) {
+            xv = bp[L::at(idx)];
+          } else {
+            const Cx<T> c = bp[L::at(M - idx)];
+            xv = {-c.x, -c.y};
+          }
+        } else if constexpr (FIRST) {
+          if (idx == 0) {
             xv = {T(0), T(0)};
           } else {
             const Cx<T> c = bp[L::at(idx)], d = bp[L::at(N - idx)];
@@ -228,7 +253,7 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
         } else {
           xv = bp[L::at(idx)];
         }
-        if (NS > 1 && r > 0) xv = cmul(xv, tw[(jj % NS) * r * (N / (NS * R))]);
+        if (NS > 1 && r > 0) xv = cmul(xv, tw[(jj % NS) * r * (M / (NS * R))]);
         v[q][r] = xv;
       }
       Dft<T, R>::run(v[q]);
@@ -240,17 +265,27 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
     const int jj = l + TPP * q;
     if (TP % TPP == 0 || jj < TP) {
       const int base = (jj / NS) * NS * R + (jj % NS);
+      if constexpr (LAST && L::ODD) {
+        static_assert(R % 2 == 0 && NS * R == M, "last ODD radix must be even");
 #pragma unroll
-      for (int r = 0; r < R; ++r) bp[L::at(base + r * NS)] = v[q][r];
+        for (int r = 0; r < R / 2; ++r) {   // k = jj + r*NS < N
+          const Cx<T> z = v[q][r];
+          const int k = base + r * NS;
+          bp[L::at(k)] = (k == 0) ? Cx<T>{T(0), T(0)} : Cx<T>{sc * z.y, -sc * z.x};
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) bp[L::at(base + r * NS)] = v[q][r];
+      }
     }
   }
   __syncthreads();
-  if constexpr (sizeof...(Rest) > 0) stockham<T, N, NS * R, false, Rest...>(bp, tw, sn, l);
+  if constexpr (!LAST) stockham<T, N, NS * R, false, Rest...>(bp, tw, sn, l, sc);
 }
 
 template <class T, int N, int... Rs>
-__device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, Radices<Rs...>) {
-  stockham<T, N, 1, true, Rs...>(bp, tw, sn, l);
+__device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, T sc, Radices<Rs...>) {
+  stockham<T, N, 1, true, Rs...>(bp, tw, sn, l, sc);
 }
 
 // `mask` names the lanes of the warp that exist (a CTA may have fewer than 32 threads).
@@ -259,67 +294,74 @@ __device__ __forceinline__ Cx<T> shfl_up_cx(unsigned mask, Cx<T> v, int d, int w
   return {__shfl_up_sync(mask, v.x, d, width), __shfl_up_sync(mask, v.y, d, width)};
 }
 
-// Full DST-I of the pair at bp (in place); sc = sqrt(2/N)/2. `epi(j, w)` receives the scaled
-// result w at position j
-// (j = 0..N-1, w = 0 at j = 0) after every read of the pair has completed, and returns the value
-// stored at j; it may also read or write other buffers at the same (pair, j).
-// `scr` is shared scratch of TPP/32 complex per pair (used only when TPP > 32).
-template <class T, int N, class Epi>
+// Full orthonormal DST-I of the pair at bp, in place: on return positions 0..N-1 hold the result
+// (position 0 = 0). sc = sqrt(2/N)/2. tw holds the M-th roots of unity, sn = sin(pi j / N)
+// (recurrence only). `scr` is shared scratch of TPP/32 complex per pair (recurrence, TPP > 32).
+template <class T, int N>
 __device__ __forceinline__ void dst_pair(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
-                                         const T* __restrict__ sn, int l, Cx<T>* scr, T sc, Epi&& epi) {
+                                         const T* __restrict__ sn, int l, Cx<T>* scr, T sc) {
   using L = PairLayout<T, N>;
-  constexpr int TPP = L::TPP;
-  constexpr int C = (N / 2) / TPP;
-  static_assert(C * TPP == N / 2, "N/2 must be a multiple of the threads per pair");
-  run_fft<T, N>(bp, tw, sn, l, typename FftPlan<T, N>::R{});
-
-  Cx<T> g[C], e[C];
+  run_fft<T, N>(bp, tw, sn, l, sc, typename FftPlan<T, N>::R{});
+  if constexpr (!L::ODD) {
+    constexpr int TPP = L::TPP;
+    constexpr int C = (N / 2) / TPP;
+    static_assert(C * TPP == N / 2, "N/2 must be a multiple of the threads per pair");
+    Cx<T> g[C], e[C];
 #pragma unroll
-  for (int i = 0; i < C; ++i) {
-    const int m = l * C + i;
-    const Cx<T> zm = bp[L::at(m)];
-    if (m == 0) {
-      g[i] = zm;
-      e[i] = {T(0), T(0)};
-    } else {
-      const Cx<T> zn = bp[L::at(N - m)];
-      g[i] = zm + zn;
-      const Cx<T> d = zm - zn;
-      e[i] = {d.y, -d.x};
+    for (int i = 0; i < C; ++i) {
+      const int m = l * C + i;
+      const Cx<T> zm = bp[L::at(m)];
+      if (m == 0) {
+        g[i] = zm;
+        e[i] = {T(0), T(0)};
+      } else {
+        const Cx<T> zn = bp[L::at(N - m)];
+        g[i] = zm + zn;
+        const Cx<T> d = zm - zn;
+        e[i] = {d.y, -d.x};
+      }
+      if (i > 0) g[i] = g[i] + g[i - 1];
     }
-    if (i > 0) g[i] = g[i] + g[i - 1];
-  }
-  // exclusive offset of this lane's chunk within the pair
-  constexpr int W = TPP < 32 ? TPP : 32;
-  const Cx<T> tot = g[C - 1];
-  Cx<T> inc = tot;
-  const int ls = l % W;
-  const unsigned mask = __activemask();  // every thread of the CTA reaches this point converged
+    // exclusive offset of this lane's chunk within the pair
+    constexpr int W = TPP < 32 ? TPP : 32;
+    const Cx<T> tot = g[C - 1];
+    Cx<T> inc = tot;
+    const int ls = l % W;
+    const unsigned mask = __activemask();  // every thread of the CTA reaches this point converged
 #pragma unroll
-  for (int d = 1; d < W; d <<= 1) {
-    const Cx<T> t = shfl_up_cx(mask, inc, d, W);
-    if (ls >= d) inc = inc + t;
-  }
-  if constexpr (TPP > 32) {
-    constexpr int NW = TPP / 32;
-    const int w = l / 32;
-    if (ls == 31) scr[w] = inc;
+    for (int d = 1; d < W; d <<= 1) {
+      const Cx<T> t = shfl_up_cx(mask, inc, d, W);
+      if (ls >= d) inc = inc + t;
+    }
+    if constexpr (TPP > 32) {
+      constexpr int NW = TPP / 32;
+      const int w = l / 32;
+      if (ls == 31) scr[w] = inc;
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NW - 1; ++k)
+        if (k < w) inc = inc + scr[k];
+    } else {
+      __syncthreads();
+    }
+    const Cx<T> off = inc - tot;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int m = l * C + i;
+      bp[L::at(2 * m)] = (m == 0) ? Cx<T>{T(0), T(0)} : sc * e[i];
+      bp[L::at(2 * m + 1)] = sc * (g[i] + off);
+    }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NW - 1; ++k)
-      if (k < w) inc = inc + scr[k];
-  } else {
-    __syncthreads();
   }
-  const Cx<T> off = inc - tot;
-#pragma unroll
-  for (int i = 0; i < C; ++i) {
-    const int m = l * C + i;
-    const Cx<T> w0 = (m == 0) ? Cx<T>{T(0), T(0)} : sc * e[i];
-    const Cx<T> w1 = sc * (g[i] + off);
-    bp[L::at(2 * m)] = epi(2 * m, w0);
-    bp[L::at(2 * m + 1)] = epi(2 * m + 1, w1);
-  }
+}
+
+// Pointwise epilogue over positions 0..N-1 of one pair: bp[j] = epi(j, bp[j]). The loop is kept
+// rolled so that the epilogue's code appears once in the kernel.
+template <class T, int N, class Epi>
+__device__ __forceinline__ void epilogue_pair(Cx<T>* __restrict__ bp, int l, Epi&& epi) {
+  using L = PairLayout<T, N>;
+#pragma unroll 1
+  for (int j = l; j < N; j += L::TPP) bp[L::at(j)] = epi(j, bp[L::at(j)]);
   __syncthreads();
 }
 

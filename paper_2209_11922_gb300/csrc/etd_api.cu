@@ -158,7 +158,7 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   a.sn = static_cast<const T*>(pl->sn[axis]);
   a.sc = (T)pl->sc[axis];
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
-  const int maxp = 256 / k->tpp > 0 ? 256 / k->tpp : 1;
+  const int maxp = 512 / k->tpp > 0 ? 512 / k->tpp : 1;
   int P = 1;
   long long grid = 0;
   if (axis == 0) {
@@ -285,22 +285,29 @@ etd_status entry_exit_any(etd_plan_s* pl, bool entry, void* u, std::vector<Launc
 
 template <class T>
 etd_status upload_tables(etd_plan_s* pl) {
-  // FP64 on the host, rounded once to T: per axis tw (2N), sn (N), zeta, ex, ec (N each)
+  // FP64 on the host, rounded once to T: per axis tw (2M, M = FFT length), sn, zeta, ex, ec (N each)
+  int fftM[3] = {0, 0, 0};
   size_t total = 0;
-  for (int a = 0; a < pl->ndim; ++a) total += 6 * (size_t)pl->N[a];
+  for (int a = 0; a < pl->ndim; ++a) {
+    const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a]);
+    if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %lld", (long long)pl->N[a]);
+    fftM[a] = k->fft_len;
+    total += 2 * (size_t)fftM[a] + 4 * (size_t)pl->N[a];
+  }
   std::vector<T> h(total);
   size_t off = 0;
   size_t offs[3][5];
   for (int a = 0; a < pl->ndim; ++a) {
     const int n = (int)pl->N[a];
     const double hh = pl->h[a];
+    const int M = fftM[a];
     offs[a][0] = off;
-    for (int m = 0; m < n; ++m) {
-      const double ang = 2.0 * M_PI * (double)m / (double)n;
+    for (int m = 0; m < M; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / (double)M;
       h[off + 2 * m] = (T)cos(ang);
       h[off + 2 * m + 1] = (T)sin(ang);
     }
-    off += 2 * (size_t)n;
+    off += 2 * (size_t)M;
     offs[a][1] = off;
     for (int j = 0; j < n; ++j) h[off + j] = (T)sin(M_PI * (double)j / (double)n);
     off += n;

@@ -45,8 +45,8 @@ template <class T> struct PassArgs {
   const T* in1;
   T* out0;
   T* out1;
-  const T* tw;      // exp(2 pi i m / N), m < N, interleaved (re, im), of the transformed axis
-  const T* sn;      // sin(pi j / N), j < N
+  const T* tw;      // exp(2 pi i m / M), m < M (M = FFT length), interleaved (re, im)
+  const T* sn;      // sin(pi j / N), j < N (recurrence variant only)
   const T* zeta[3]; // per paper axis: tau D mu_a
   const T* ex[3];   // exp(-tau D mu_a)
   const T* ec[3];   // exp(-c2 tau D mu_a)
@@ -100,7 +100,7 @@ template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
 
 template <class T, int N>
-__global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> A) {
+__global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
   using L = PairLayout<T, N>;
   using C = Cx<T>;
   using VT = typename V2<T>::type;
@@ -269,56 +269,58 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<T> A) {
   C* const scrp = scr + p * (TPP > 32 ? TPP / 32 : 1);
   const T tau = A.tau, c2 = A.c2, flin = A.flin, fcub = A.fcub;
 
-  for (int s = 0; s < nd; ++s) {
-    const int kind = epi[s];
-    C* bp = bsel[s] ? b1p : b0p;
-    dst_pair<T, N>(bp, tw, sn, l, scrp, A.sc, [&](int j, C w) -> C {
-      if (kind == EPI_PLAIN) return w;
-      if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
-      const T zjj = zj[j], ejj = ej[j];
-      T out[2];
-      const T wv[2] = {w.x, w.y};
-      if (kind == EPI_RK1) {
-        const C u = b0p[L::at(j)];
-        const T uv[2] = {u.x, u.y};
-        T nv[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const T zeta = pz[t] + zjj, E = pe[t] * ejj;
-          nv[t] = E * uv[t] + tau * phi1_only(zeta, E) * wv[t];
-        }
-        b0p[L::at(j)] = C{nv[0], nv[1]};
-        return w;
-      }
-      if (kind == EPI_S1) {
-        const T cjj = cj[j];
-        const C u = b0p[L::at(j)];
-        const T uv[2] = {u.x, u.y};
-        T u2[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj;
-          T p1, p2;
-          phi12(zeta, E, p1, p2);
-          const T p1c = phi1_only(c2 * zeta, Ec);
-          u2[t] = Ec * uv[t] + c2 * tau * p1c * wv[t];
-          out[t] = E * uv[t] + tau * (p1 - p2 / c2) * wv[t];
-        }
-        b0p[L::at(j)] = C{u2[0], u2[1]};
-        return C{out[0], out[1]};
-      }
-      // EPI_S2: P from the second buffer
-      const C pp = b1p[L::at(j)];
-      const T pv[2] = {pp.x, pp.y};
+  auto epilogue = [&](int kind, int j, C w) -> C {
+    if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
+    const T zjj = zj[j], ejj = ej[j];
+    T out[2];
+    const T wv[2] = {w.x, w.y};
+    if (kind == EPI_RK1) {
+      const C u = b0p[L::at(j)];
+      const T uv[2] = {u.x, u.y};
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const T zeta = pz[t] + zjj, E = pe[t] * ejj;
+        out[t] = E * uv[t] + tau * phi1_only(zeta, E) * wv[t];
+      }
+      b0p[L::at(j)] = C{out[0], out[1]};
+      return w;
+    }
+    if (kind == EPI_S1) {
+      const T cjj = cj[j];
+      const C u = b0p[L::at(j)];
+      const T uv[2] = {u.x, u.y};
+      T u2[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj;
         T p1, p2;
         phi12(zeta, E, p1, p2);
-        out[t] = pv[t] + (tau / c2) * p2 * wv[t];
+        const T p1c = phi1_only(c2 * zeta, Ec);
+        u2[t] = Ec * uv[t] + c2 * tau * p1c * wv[t];
+        out[t] = E * uv[t] + tau * (p1 - p2 / c2) * wv[t];
       }
+      b0p[L::at(j)] = C{u2[0], u2[1]};
       return C{out[0], out[1]};
-    });
+    }
+    // EPI_S2: P from the second buffer
+    const C pp = b1p[L::at(j)];
+    const T pv[2] = {pp.x, pp.y};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const T zeta = pz[t] + zjj, E = pe[t] * ejj;
+      T p1, p2;
+      phi12(zeta, E, p1, p2);
+      out[t] = pv[t] + (tau / c2) * p2 * wv[t];
+    }
+    return C{out[0], out[1]};
+  };
+
+#pragma unroll 1
+  for (int s = 0; s < nd; ++s) {
+    const int kind = epi[s];
+    C* bp = bsel[s] ? b1p : b0p;
+    dst_pair<T, N>(bp, tw, sn, l, scrp, A.sc);
+    if (kind != EPI_PLAIN) epilogue_pair<T, N>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
 
@@ -333,11 +335,12 @@ struct KernelInfo {
   int tpp;
   int lp;
   int elem;   // sizeof(T)
+  int fft_len;  // M: 2N (odd extension) or N (recurrence)
 };
 
 template <class T, int N> KernelInfo kernel_info() {
   using L = PairLayout<T, N>;
-  return KernelInfo{reinterpret_cast<const void*>(&pass_kernel<T, N>), N, L::TPP, L::LP, (int)sizeof(T)};
+  return KernelInfo{reinterpret_cast<const void*>(&pass_kernel<T, N>), N, L::TPP, L::LP, (int)sizeof(T), L::M};
 }
 
 // shared memory bytes of a launch
