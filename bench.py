@@ -166,7 +166,7 @@ def run_gb300(args, w):
     dtype = args.dtype
     tdt = torch.float32 if dtype == "f32" else torch.float64
     nsteps = args.time_steps or w.nsteps
-    plan = Plan(w.N, w.D, w.tau, scheme=w.scheme, dtype=dtype)
+    plan = Plan(w.N, w.D, w.tau, scheme=w.scheme, dtype=dtype, route=args.route)
     info = plan.info()
     u0 = torch.from_numpy(w.u0().astype(np.float32 if dtype == "f32" else np.float64)).cuda()
     u = torch.empty_like(u0)
@@ -250,7 +250,7 @@ def run_gb300(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": w.name, "mesh": list(w.N), "unknowns": w.unknowns, "time_steps_per_step": nsteps,
+            "config": {"workload": w.name, "route": args.route, "mesh": list(w.N), "unknowns": w.unknowns, "time_steps_per_step": nsteps,
                        "D": w.D, "tau": w.tau, "scheme": "ETDRK2" if w.scheme == 2 else "ETDRK1",
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written between bench steps; within one run the fields stay L2-resident",
@@ -284,6 +284,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=inputs.AC2D_1024.name, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--route", default="auto", choices=["auto", "fft", "fft_half"])
     ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time-step count")
     ap.add_argument("--ref-sample-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -46,7 +46,12 @@ typedef enum {
 
 typedef enum { ETD_ETDRK1 = 1, ETD_ETDRK2 = 2 } etd_scheme;   /* EIFE1 eq. (2.13), EIFE2 eq. (2.14) */
 typedef enum { ETD_F64 = 0, ETD_F32 = 1 } etd_dtype;            /* arithmetic and storage type of u */
-typedef enum { ETD_ROUTE_AUTO = 0, ETD_ROUTE_FFT = 1 } etd_route; /* transform implementation */
+/* Transform implementation of the DST-I along each axis.
+ * ETD_ROUTE_FFT: FP32 uses the odd extension (a length-2N complex FFT per pair of pencils; rounding
+ *   grows like log N); FP64 uses the half-length recurrence below.
+ * ETD_ROUTE_FFT_HALF: a length-N complex FFT per pair of pencils followed by a prefix sum (half the
+ *   work; rounding grows like sqrt(N/2) eps). ETD_ROUTE_AUTO = ETD_ROUTE_FFT. */
+typedef enum { ETD_ROUTE_AUTO = 0, ETD_ROUTE_FFT = 1, ETD_ROUTE_FFT_HALF = 2 } etd_route;
 
 typedef struct {
   etd_dtype dtype;   /* default ETD_F64 */

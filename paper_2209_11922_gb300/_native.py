@@ -18,7 +18,7 @@ c_int, c_double, c_int64, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, c
 
 ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD_ERR_NONFINITE = range(6)
 ETD_F64, ETD_F32 = 0, 1
-ETD_ROUTE_AUTO, ETD_ROUTE_FFT = 0, 1
+ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF = 0, 1, 2
 ETD_NUM_PASS_KINDS = 8
 
 

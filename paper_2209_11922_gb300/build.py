@@ -51,26 +51,29 @@ def generate() -> list:
     srcs = []
     decls, rows = [], []
     for tk, tn in TYPES.items():
-        for n in LENGTHS:
-            name = f"kinfo_{tk}_{n}"
-            path = os.path.join(GEN, f"inst_{tk}_{n}.cu")
-            _write_if_changed(path, (
-                '#include "pass_kernel.cuh"\n'
-                "namespace etd {\n"
-                f"template __global__ void pass_kernel<{tn}, {n}>(const PassArgs<{tn}>);\n"
-                f"KernelInfo {name}() {{ return kernel_info<{tn}, {n}>(); }}\n"
-                "}  // namespace etd\n"))
-            srcs.append(path)
-            decls.append(f"KernelInfo {name}();")
-            rows.append(f"    {name}(),")
+        for odd in ((True, False) if tk == "f32" else (False,)):
+            for n in LENGTHS:
+                v = "odd" if odd else "rec"
+                o = "true" if odd else "false"
+                name = f"kinfo_{tk}_{v}_{n}"
+                path = os.path.join(GEN, f"inst_{tk}_{v}_{n}.cu")
+                _write_if_changed(path, (
+                    '#include "pass_kernel.cuh"\n'
+                    "namespace etd {\n"
+                    f"template __global__ void pass_kernel<{tn}, {n}, {o}>(const PassArgs<{tn}>);\n"
+                    f"KernelInfo {name}() {{ return kernel_info<{tn}, {n}, {o}>(); }}\n"
+                    "}  // namespace etd\n"))
+                srcs.append(path)
+                decls.append(f"KernelInfo {name}();")
+                rows.append(f"    {name}(),")
     reg = os.path.join(GEN, "registry.cu")
     _write_if_changed(reg, (
         '#include "pass_kernel.cuh"\n'
         "namespace etd {\n" + "\n".join(decls) + "\n"
-        "const KernelInfo* find_pass_kernel(int elem, int N) {\n"
+        "const KernelInfo* find_pass_kernel(int elem, int N, int odd) {\n"
         "  static const KernelInfo table[] = {\n" + "\n".join(rows) + "\n  };\n"
         "  for (const KernelInfo& k : table)\n"
-        "    if (k.elem == elem && k.N == N) return &k;\n"
+        "    if (k.elem == elem && k.N == N && k.odd == odd) return &k;\n"
         "  return nullptr;\n"
         "}\n"
         "}  // namespace etd\n"))

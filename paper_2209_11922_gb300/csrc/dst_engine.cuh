@@ -146,9 +146,9 @@ __device__ __forceinline__ void Dft<T, R>::run(Cx<T>* x) {
 // A thread holds at most 32 (FP32) / 16 (FP64) complex values in a pass; the last radix of an ODD
 // plan is even so that the outputs k < N are exactly the butterfly outputs r < R/2.
 template <int... Rs> struct Radices {};
-template <class T, int N> struct FftPlan;
+template <class T, int N, bool ODD> struct FftPlan;
 #define ETD_PLAN(TYPE, NN, ODD_, TPP_, ...)                \
-  template <> struct FftPlan<TYPE, NN> {                   \
+  template <> struct FftPlan<TYPE, NN, ODD_> {             \
     static constexpr bool ODD = ODD_;                      \
     static constexpr int M = ODD_ ? 2 * NN : NN;           \
     static constexpr int TPP = TPP_;                       \
@@ -174,7 +174,26 @@ ETD_PLAN(float, 192, true, 64, 6, 4, 16)
 ETD_PLAN(float, 384, true, 64, 12, 4, 16)
 ETD_PLAN(float, 768, true, 128, 12, 8, 16)
 ETD_PLAN(float, 1536, true, 256, 12, 16, 16)
-// FP64: recurrence, M = N
+// FP32 and FP64: recurrence, M = N
+ETD_PLAN(float, 4, false, 1, 4)
+ETD_PLAN(float, 8, false, 2, 4, 2)
+ETD_PLAN(float, 16, false, 4, 4, 4)
+ETD_PLAN(float, 32, false, 4, 8, 4)
+ETD_PLAN(float, 64, false, 8, 8, 8)
+ETD_PLAN(float, 128, false, 8, 16, 8)
+ETD_PLAN(float, 256, false, 16, 16, 16)
+ETD_PLAN(float, 512, false, 64, 8, 8, 8)
+ETD_PLAN(float, 1024, false, 128, 8, 8, 16)
+ETD_PLAN(float, 2048, false, 128, 16, 8, 16)
+ETD_PLAN(float, 6, false, 1, 6)
+ETD_PLAN(float, 12, false, 2, 4, 3)
+ETD_PLAN(float, 24, false, 4, 8, 3)
+ETD_PLAN(float, 48, false, 4, 12, 4)
+ETD_PLAN(float, 96, false, 8, 12, 8)
+ETD_PLAN(float, 192, false, 16, 12, 16)
+ETD_PLAN(float, 384, false, 32, 8, 3, 16)
+ETD_PLAN(float, 768, false, 64, 16, 3, 16)
+ETD_PLAN(float, 1536, false, 128, 16, 6, 16)
 ETD_PLAN(double, 4, false, 1, 4)
 ETD_PLAN(double, 8, false, 2, 4, 2)
 ETD_PLAN(double, 16, false, 4, 4, 4)
@@ -199,8 +218,8 @@ ETD_PLAN(double, 1536, false, 128, 16, 6, 16)
 template <class L> struct FirstRadix;
 template <int R0, int... Rs> struct FirstRadix<Radices<R0, Rs...>> { static constexpr int value = R0; };
 
-template <class T, int N> struct PairLayout {
-  using Plan = FftPlan<T, N>;
+template <class T, int N, bool ODD_> struct PairLayout {
+  using Plan = FftPlan<T, N, ODD_>;
   static constexpr bool ODD = Plan::ODD;
   static constexpr int M = Plan::M;
   static constexpr int TPP = Plan::TPP;
@@ -215,10 +234,10 @@ template <class T, int N> struct PairLayout {
 // (jj/Ns)*Ns*R + (jj mod Ns) + r*Ns. In place: all reads, barrier, all writes, barrier.
 // The first pass folds in the input map of the variant (odd extension or the y_j of the
 // recurrence); the last pass of the ODD variant writes only k < N, already scaled by -i sc.
-template <class T, int N, int NS, bool FIRST, int R, int... Rest>
+template <class T, int N, bool ODD, int NS, bool FIRST, int R, int... Rest>
 __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
                                          const T* __restrict__ sn, int l, T sc) {
-  using L = PairLayout<T, N>;
+  using L = PairLayout<T, N, ODD>;
   constexpr int M = L::M;
   constexpr int TPP = L::TPP;
   constexpr int TP = M / R;
@@ -280,12 +299,12 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
     }
   }
   __syncthreads();
-  if constexpr (!LAST) stockham<T, N, NS * R, false, Rest...>(bp, tw, sn, l, sc);
+  if constexpr (!LAST) stockham<T, N, ODD, NS * R, false, Rest...>(bp, tw, sn, l, sc);
 }
 
-template <class T, int N, int... Rs>
+template <class T, int N, bool ODD, int... Rs>
 __device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, T sc, Radices<Rs...>) {
-  stockham<T, N, 1, true, Rs...>(bp, tw, sn, l, sc);
+  stockham<T, N, ODD, 1, true, Rs...>(bp, tw, sn, l, sc);
 }
 
 // `mask` names the lanes of the warp that exist (a CTA may have fewer than 32 threads).
@@ -297,11 +316,11 @@ __device__ __forceinline__ Cx<T> shfl_up_cx(unsigned mask, Cx<T> v, int d, int w
 // Full orthonormal DST-I of the pair at bp, in place: on return positions 0..N-1 hold the result
 // (position 0 = 0). sc = sqrt(2/N)/2. tw holds the M-th roots of unity, sn = sin(pi j / N)
 // (recurrence only). `scr` is shared scratch of TPP/32 complex per pair (recurrence, TPP > 32).
-template <class T, int N>
+template <class T, int N, bool ODD>
 __device__ __forceinline__ void dst_pair(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
                                          const T* __restrict__ sn, int l, Cx<T>* scr, T sc) {
-  using L = PairLayout<T, N>;
-  run_fft<T, N>(bp, tw, sn, l, sc, typename FftPlan<T, N>::R{});
+  using L = PairLayout<T, N, ODD>;
+  run_fft<T, N, ODD>(bp, tw, sn, l, sc, typename FftPlan<T, N, ODD>::R{});
   if constexpr (!L::ODD) {
     constexpr int TPP = L::TPP;
     constexpr int C = (N / 2) / TPP;
@@ -357,9 +376,9 @@ __device__ __forceinline__ void dst_pair(Cx<T>* __restrict__ bp, const Cx<T>* __
 
 // Pointwise epilogue over positions 0..N-1 of one pair: bp[j] = epi(j, bp[j]). The loop is kept
 // rolled so that the epilogue's code appears once in the kernel.
-template <class T, int N, class Epi>
+template <class T, int N, bool ODD, class Epi>
 __device__ __forceinline__ void epilogue_pair(Cx<T>* __restrict__ bp, int l, Epi&& epi) {
-  using L = PairLayout<T, N>;
+  using L = PairLayout<T, N, ODD>;
 #pragma unroll 1
   for (int j = l; j < N; j += L::TPP) bp[L::at(j)] = epi(j, bp[L::at(j)]);
   __syncthreads();

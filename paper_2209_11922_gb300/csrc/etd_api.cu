@@ -27,7 +27,7 @@
 
 namespace etd {
 // registry of instantiated pass kernels (generated per (type, N) translation units)
-const KernelInfo* find_pass_kernel(int elem, int N);
+const KernelInfo* find_pass_kernel(int elem, int N, int odd);
 }  // namespace etd
 
 using namespace etd;
@@ -93,6 +93,7 @@ struct etd_plan_s {
   int scheme = 2;
   etd_options opt{};
   int elem = 8;
+  int odd = 0;             // DST variant: 1 odd extension (FP32 default), 0 half-length recurrence
   int nx = 1, ny = 1, nz = 1;
   size_t nfield = 0;       // pitched elements per field
   int64_t unknowns = 0;    // interior unknowns
@@ -144,7 +145,7 @@ template <class T>
 etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const void* in1, void* out0,
                        void* out1, int kind, double fields_rw, Launch& L) {
   const int N = (int)pl->N[axis];
-  const KernelInfo* k = find_pass_kernel((int)sizeof(T), N);
+  const KernelInfo* k = find_pass_kernel((int)sizeof(T), N, pl->odd);
   if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", N);
   PassArgs<T> a;
   fill_common<T>(pl, a);
@@ -289,7 +290,7 @@ etd_status upload_tables(etd_plan_s* pl) {
   int fftM[3] = {0, 0, 0};
   size_t total = 0;
   for (int a = 0; a < pl->ndim; ++a) {
-    const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a]);
+    const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a], pl->odd);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %lld", (long long)pl->N[a]);
     fftM[a] = k->fft_len;
     total += 2 * (size_t)fftM[a] + 4 * (size_t)pl->N[a];
@@ -425,7 +426,8 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   if (!(std::isfinite(o.c2) && o.c2 > 0 && o.c2 <= 1)) return fail(ETD_ERR_INVALID_ARG, "c2 must lie in (0, 1]");
   if (!std::isfinite(o.flin) || !std::isfinite(o.fcub)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
   if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
-  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT) return fail(ETD_ERR_INVALID_ARG, "unknown route");
+  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF)
+    return fail(ETD_ERR_INVALID_ARG, "unknown route");
   for (int a = 0; a < ndim; ++a) {
     if (N[a] < 2) return fail(ETD_ERR_INVALID_ARG, "N[%d] = %lld < 2", a, (long long)N[a]);
     if (N[a] % 2) return fail(ETD_ERR_INVALID_ARG, "N[%d] = %lld must be even", a, (long long)N[a]);
@@ -446,6 +448,7 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   pl->scheme = scheme;
   pl->opt = o;
   pl->elem = (o.dtype == ETD_F32) ? 4 : 8;
+  pl->odd = (o.dtype == ETD_F32 && o.route != ETD_ROUTE_FFT_HALF) ? 1 : 0;
   pl->nx = (int)N[0];
   pl->ny = (int)N[1];
   pl->nz = ndim == 3 ? (int)N[2] : 1;

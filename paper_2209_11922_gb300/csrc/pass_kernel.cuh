@@ -99,17 +99,19 @@ template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
 
-template <class T, int N>
+template <class T, int N, bool ODD>
 __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
-  using L = PairLayout<T, N>;
+  using L = PairLayout<T, N, ODD>;
   using C = Cx<T>;
   using VT = typename V2<T>::type;
   constexpr int TPP = L::TPP;
   constexpr int LP = L::LP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const C* __restrict__ tw = reinterpret_cast<const C*>(A.tw);
+  // shared memory: M twiddles, then the tile buffers, then scan scratch
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  const C* __restrict__ tw = tws;
   const T* __restrict__ sn = A.sn;
-  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b0 = tws + L::M;
   const int op = A.op;
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
   C* b1 = b0 + A.P * LP;
@@ -214,14 +216,18 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
     }
   };
 
-  // ---- loads
+  // ---- loads (twiddles of the transformed axis, then the tile)
+  if (op != OP_PACK && op != OP_UNPACK) {
+    const C* gtw = reinterpret_cast<const C*>(A.tw);
+    for (int i = tid; i < L::M; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
+  }
   if (op == OP_ENTRY || op == OP_PACK) {
     load_dense(A.in0, b0);
   } else {
     load_tile(A.in0, b0);
     if (two) load_tile(A.in1, b1);
-    cp_async_wait_all();
   }
+  cp_async_wait_all();
   __syncthreads();
 
   if (op == OP_PACK) {
@@ -319,8 +325,8 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
   for (int s = 0; s < nd; ++s) {
     const int kind = epi[s];
     C* bp = bsel[s] ? b1p : b0p;
-    dst_pair<T, N>(bp, tw, sn, l, scrp, A.sc);
-    if (kind != EPI_PLAIN) epilogue_pair<T, N>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
+    dst_pair<T, N, ODD>(bp, tw, sn, l, scrp, A.sc);
+    if (kind != EPI_PLAIN) epilogue_pair<T, N, ODD>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
 
@@ -336,19 +342,22 @@ struct KernelInfo {
   int lp;
   int elem;   // sizeof(T)
   int fft_len;  // M: 2N (odd extension) or N (recurrence)
+  int odd;      // 1: odd-extension variant, 0: recurrence variant
 };
 
-template <class T, int N> KernelInfo kernel_info() {
-  using L = PairLayout<T, N>;
-  return KernelInfo{reinterpret_cast<const void*>(&pass_kernel<T, N>), N, L::TPP, L::LP, (int)sizeof(T), L::M};
+template <class T, int N, bool ODD> KernelInfo kernel_info() {
+  using L = PairLayout<T, N, ODD>;
+  return KernelInfo{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
+                    ODD ? 1 : 0};
 }
 
 // shared memory bytes of a launch
 inline size_t pass_smem_bytes(const KernelInfo& k, int P, int nbuf) {
   const size_t c = 2 * (size_t)k.elem;
+  const size_t tw = (size_t)k.fft_len * c;
   const size_t bufs = (size_t)nbuf * P * k.lp * c;
   const size_t scr = (size_t)P * (k.tpp > 32 ? k.tpp / 32 : 1) * c;
-  return bufs + scr;
+  return tw + bufs + scr;
 }
 
 }  // namespace etd

@@ -13,6 +13,7 @@ import numpy as np
 from . import _native as nat
 
 _DT = {"f64": nat.ETD_F64, "f32": nat.ETD_F32}
+_ROUTE = {"auto": nat.ETD_ROUTE_AUTO, "fft": nat.ETD_ROUTE_FFT, "fft_half": nat.ETD_ROUTE_FFT_HALF}
 
 
 def _torch():
@@ -35,7 +36,8 @@ class Plan:
     """
 
     def __init__(self, N: Sequence[int], D: float, tau: float, scheme: int = 2, dtype: str = "f64",
-                 h: Optional[Sequence[float]] = None, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0):
+                 h: Optional[Sequence[float]] = None, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0,
+                 route: str = "auto"):
         L = nat.lib()
         self.N = tuple(int(n) for n in N)
         self.ndim = len(self.N)
@@ -46,6 +48,7 @@ class Plan:
         opt = nat.EtdOptions()
         L.etd_options_default(ctypes.byref(opt))
         opt.dtype = _DT[dtype]
+        opt.route = _ROUTE[route]
         opt.c2, opt.flin, opt.fcub = float(c2), float(flin), float(fcub)
         Na = (ctypes.c_int64 * 3)(*(list(self.N) + [1] * (3 - self.ndim)))
         ha = (ctypes.c_double * 3)(*(list(self.h) + [1.0] * (3 - self.ndim)))
