@@ -194,9 +194,15 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   memcpy(L.args, &a, sizeof(a));
   L.args_size = sizeof(a);
   L.alg_bytes = fields_rw * (double)pl->unknowns * sizeof(T);
+  // One kernel serves every axis of a given length, with different tile sizes, so the opt-in
+  // limit is raised to the device maximum (not to this launch's size, which a later launch of the
+  // same kernel could then undercut).
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+  if (L.smem > (size_t)optin) return fail(ETD_ERR_UNSUPPORTED, "tile needs %zu B of shared memory (max %d)", L.smem, optin);
   if (L.smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-    if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "cudaFuncSetAttribute(%zu B): %s", L.smem, cudaGetErrorString(e));
+    cudaError_t e = cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "cudaFuncSetAttribute(%d B): %s", optin, cudaGetErrorString(e));
   }
   return ETD_OK;
 }
