@@ -50,7 +50,9 @@ typedef enum { ETD_F64 = 0, ETD_F32 = 1 } etd_dtype;            /* arithmetic an
  * ETD_ROUTE_FFT: FP32 uses the odd extension (a length-2N complex FFT per pair of pencils; rounding
  *   grows like log N); FP64 uses the half-length recurrence below.
  * ETD_ROUTE_FFT_HALF: a length-N complex FFT per pair of pencils followed by a prefix sum (half the
- *   work; rounding grows like sqrt(N/2) eps). ETD_ROUTE_AUTO = ETD_ROUTE_FFT. */
+ *   work; rounding grows like sqrt(N/2) eps).
+ * ETD_ROUTE_AUTO: per axis, FP32 takes ETD_ROUTE_FFT for N >= 512 and ETD_ROUTE_FFT_HALF below;
+ *   FP64 always takes the recurrence. */
 typedef enum { ETD_ROUTE_AUTO = 0, ETD_ROUTE_FFT = 1, ETD_ROUTE_FFT_HALF = 2 } etd_route;
 
 typedef struct {

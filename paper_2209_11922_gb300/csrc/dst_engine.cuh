@@ -224,9 +224,20 @@ template <class T, int N, bool ODD_> struct PairLayout {
   static constexpr int M = Plan::M;
   static constexpr int TPP = Plan::TPP;
   static constexpr int PADG = FirstRadix<typename Plan::R>::value;
-  static constexpr int LP = M + M / PADG + 1;  // complex slots per pair
+  static constexpr int LP = M + M / PADG + 1;  // minimum complex slots per pair
+  static constexpr int TWN = TwiddleCount<typename Plan::R>::value;  // twiddle table entries
   static __device__ __forceinline__ int at(int j) { return j + j / PADG; }
 };
+
+// Twiddle tables: for every pass after the first (NS > 1) the factors w_M^{k r M/(NS R)},
+// k = jj mod NS < NS, r = 1..R-1, are stored r-major at [(r-1)*NS + k], passes back to back, so
+// the lanes of a warp (consecutive jj) read consecutive entries. TwOffset gives a pass's start.
+template <int NS, int... Rs> struct TwSize { static constexpr int value = 0; };
+template <int NS, int R, int... Rest> struct TwSize<NS, R, Rest...> {
+  static constexpr int value = (NS > 1 ? (R - 1) * NS : 0) + TwSize<NS * R, Rest...>::value;
+};
+template <class L> struct TwiddleCount;
+template <int... Rs> struct TwiddleCount<Radices<Rs...>> { static constexpr int value = TwSize<1, Rs...>::value; };
 
 // ---------------------------------------------------------------------------------------------
 // Stockham passes over the length-M sequence. Pass with radix R after Ns points are combined:
@@ -237,6 +248,7 @@ template <class T, int N, bool ODD_> struct PairLayout {
 template <class T, int N, bool ODD, int NS, bool FIRST, int R, int... Rest>
 __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
                                          const T* __restrict__ sn, int l, T sc) {
+  // tw points at this pass's table (unused when NS == 1)
   using L = PairLayout<T, N, ODD>;
   constexpr int M = L::M;
   constexpr int TPP = L::TPP;
@@ -272,7 +284,7 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
         } else {
           xv = bp[L::at(idx)];
         }
-        if (NS > 1 && r > 0) xv = cmul(xv, tw[(jj % NS) * r * (M / (NS * R))]);
+        if (NS > 1 && r > 0) xv = cmul(xv, tw[(r - 1) * NS + (jj % NS)]);
         v[q][r] = xv;
       }
       Dft<T, R>::run(v[q]);
@@ -299,7 +311,7 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
     }
   }
   __syncthreads();
-  if constexpr (!LAST) stockham<T, N, ODD, NS * R, false, Rest...>(bp, tw, sn, l, sc);
+  if constexpr (!LAST) stockham<T, N, ODD, NS * R, false, Rest...>(bp, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc);
 }
 
 template <class T, int N, bool ODD, int... Rs>

@@ -93,7 +93,7 @@ struct etd_plan_s {
   int scheme = 2;
   etd_options opt{};
   int elem = 8;
-  int odd = 0;             // DST variant: 1 odd extension (FP32 default), 0 half-length recurrence
+  int odd[3] = {0, 0, 0};  // DST variant per axis: 1 odd extension, 0 half-length recurrence
   int nx = 1, ny = 1, nz = 1;
   size_t nfield = 0;       // pitched elements per field
   int64_t unknowns = 0;    // interior unknowns
@@ -145,7 +145,7 @@ template <class T>
 etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const void* in1, void* out0,
                        void* out1, int kind, double fields_rw, Launch& L) {
   const int N = (int)pl->N[axis];
-  const KernelInfo* k = find_pass_kernel((int)sizeof(T), N, pl->odd);
+  const KernelInfo* k = find_pass_kernel((int)sizeof(T), N, pl->odd[axis]);
   if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", N);
   PassArgs<T> a;
   fill_common<T>(pl, a);
@@ -186,6 +186,7 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
     grid = (long long)a.tiles_x * other;
   }
   a.P = P;
+  a.lp = pair_stride(*k, P);
   L.fn = k->fn;
   L.grid = dim3((unsigned)grid);
   L.block = dim3((unsigned)(P * k->tpp));
@@ -294,12 +295,14 @@ template <class T>
 etd_status upload_tables(etd_plan_s* pl) {
   // FP64 on the host, rounded once to T: per axis tw (2M, M = FFT length), sn, zeta, ex, ec (N each)
   int fftM[3] = {0, 0, 0};
+  const KernelInfo* kinf[3] = {nullptr, nullptr, nullptr};
   size_t total = 0;
   for (int a = 0; a < pl->ndim; ++a) {
-    const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a], pl->odd);
+    const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a], pl->odd[a]);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %lld", (long long)pl->N[a]);
     fftM[a] = k->fft_len;
-    total += 2 * (size_t)fftM[a] + 4 * (size_t)pl->N[a];
+    kinf[a] = k;
+    total += 2 * (size_t)(k->twn > 0 ? k->twn : 1) + 4 * (size_t)pl->N[a];
   }
   std::vector<T> h(total);
   size_t off = 0;
@@ -307,14 +310,33 @@ etd_status upload_tables(etd_plan_s* pl) {
   for (int a = 0; a < pl->ndim; ++a) {
     const int n = (int)pl->N[a];
     const double hh = pl->h[a];
-    const int M = fftM[a];
+    // per-pass twiddle tables: pass with NS > 1 and radix R holds exp(2 pi i k r / (NS R)) at
+    // [(r-1)*NS + k], k < NS, r = 1..R-1 (the layout the Stockham passes read)
     offs[a][0] = off;
-    for (int m = 0; m < M; ++m) {
-      const double ang = 2.0 * M_PI * (double)m / (double)M;
-      h[off + 2 * m] = (T)cos(ang);
-      h[off + 2 * m + 1] = (T)sin(ang);
+    {
+      size_t t = 0;
+      int NS = 1;
+      for (int i = 0; i < 4 && kinf[a]->radix[i]; ++i) {
+        const int R = kinf[a]->radix[i];
+        if (NS > 1) {
+          for (int r = 1; r < R; ++r)
+            for (int k = 0; k < NS; ++k, ++t) {
+              const long long num = (long long)k * r % ((long long)NS * R);
+              const double ang = 2.0 * M_PI * (double)num / (double)(NS * R);
+              h[off + 2 * t] = (T)cos(ang);
+              h[off + 2 * t + 1] = (T)sin(ang);
+            }
+        }
+        NS *= R;
+      }
+      if (t == 0) {
+        h[off] = T(1);
+        h[off + 1] = T(0);
+        t = 1;
+      }
+      off += 2 * t;
     }
-    off += 2 * (size_t)M;
+    (void)fftM;
     offs[a][1] = off;
     for (int j = 0; j < n; ++j) h[off + j] = (T)sin(M_PI * (double)j / (double)n);
     off += n;
@@ -454,7 +476,13 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   pl->scheme = scheme;
   pl->opt = o;
   pl->elem = (o.dtype == ETD_F32) ? 4 : 8;
-  pl->odd = (o.dtype == ETD_F32 && o.route != ETD_ROUTE_FFT_HALF) ? 1 : 0;
+  for (int a = 0; a < ndim; ++a) {
+    // FP32: the odd extension keeps rounding at log N; AUTO uses it from N = 512 up and the
+    // half-length recurrence (sqrt(N/2) eps <= 11 eps) below, where it is twice as fast.
+    if (o.dtype != ETD_F32 || o.route == ETD_ROUTE_FFT_HALF) pl->odd[a] = 0;
+    else if (o.route == ETD_ROUTE_FFT) pl->odd[a] = 1;
+    else pl->odd[a] = N[a] >= 512 ? 1 : 0;
+  }
   pl->nx = (int)N[0];
   pl->ny = (int)N[1];
   pl->nz = ndim == 3 ? (int)N[2] : 1;

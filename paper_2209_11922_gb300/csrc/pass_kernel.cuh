@@ -39,6 +39,7 @@ template <class T> struct PassArgs {
   int op, axis, ndim;
   int nx, ny, nz;   // pitched extents; nz = 1 in 2D. Index 0 of each axis is the boundary / mode 0.
   int P;            // pencil pairs per CTA
+  int lp;           // complex slots per pair in shared memory (>= the layout minimum)
   int tiles_x;      // strided passes: nx / (2P)
   int npairs;       // contiguous passes: ny * nz / 2
   const T* in0;
@@ -105,13 +106,14 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
   using C = Cx<T>;
   using VT = typename V2<T>::type;
   constexpr int TPP = L::TPP;
-  constexpr int LP = L::LP;
+  const int LP = A.lp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // shared memory: M twiddles, then the tile buffers, then scan scratch
+  // shared memory: per-pass twiddle tables, then the tile buffers, then scan scratch
+  constexpr int TWN = L::TWN > 0 ? L::TWN : 1;
   C* tws = reinterpret_cast<C*>(smem_raw);
   const C* __restrict__ tw = tws;
   const T* __restrict__ sn = A.sn;
-  C* b0 = tws + L::M;
+  C* b0 = tws + ((TWN + 1) & ~1);
   const int op = A.op;
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
   C* b1 = b0 + A.P * LP;
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
   // ---- loads (twiddles of the transformed axis, then the tile)
   if (op != OP_PACK && op != OP_UNPACK) {
     const C* gtw = reinterpret_cast<const C*>(A.tw);
-    for (int i = tid; i < L::M; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
+    for (int i = tid; i < L::TWN; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
   }
   if (op == OP_ENTRY || op == OP_PACK) {
     load_dense(A.in0, b0);
@@ -343,19 +345,43 @@ struct KernelInfo {
   int elem;   // sizeof(T)
   int fft_len;  // M: 2N (odd extension) or N (recurrence)
   int odd;      // 1: odd-extension variant, 0: recurrence variant
+  int padg;     // one padding slot every padg positions
+  int twn;      // twiddle table entries
+  int radix[4]; // Stockham radices (0-terminated)
 };
+
+template <int... Rs> void radix_list(int* out, Radices<Rs...>) {
+  const int r[] = {Rs...};
+  for (int i = 0; i < 4; ++i) out[i] = i < (int)sizeof...(Rs) ? r[i] : 0;
+}
 
 template <class T, int N, bool ODD> KernelInfo kernel_info() {
   using L = PairLayout<T, N, ODD>;
-  return KernelInfo{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
-                    ODD ? 1 : 0};
+  KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
+               ODD ? 1 : 0, L::PADG, L::TWN, {0, 0, 0, 0}};
+  radix_list(k.radix, typename FftPlan<T, N, ODD>::R{});
+  return k;
+}
+
+// Pair stride for a tile of P pairs: the smallest value >= the layout minimum whose residue keeps
+// the per-row tile loads of strided passes (P lanes per row, consecutive rows) on distinct banks.
+inline int pair_stride(const KernelInfo& k, int P) {
+  const int groups = 128 / (2 * k.elem);           // complex slots per 128-byte bank cycle
+  const int want = P >= groups ? 1 : groups / P;   // residue modulo `groups`
+  int lp = k.lp;
+  if (P >= groups) {
+    if (lp % 2 == 0) ++lp;
+  } else {
+    while (lp % groups != want) ++lp;
+  }
+  return lp;
 }
 
 // shared memory bytes of a launch
 inline size_t pass_smem_bytes(const KernelInfo& k, int P, int nbuf) {
   const size_t c = 2 * (size_t)k.elem;
-  const size_t tw = (size_t)k.fft_len * c;
-  const size_t bufs = (size_t)nbuf * P * k.lp * c;
+  const size_t tw = (size_t)(((k.twn > 0 ? k.twn : 1) + 1) & ~1) * c;
+  const size_t bufs = (size_t)nbuf * P * pair_stride(k, P) * c;
   const size_t scr = (size_t)P * (k.tpp > 32 ? k.tpp / 32 : 1) * c;
   return tw + bufs + scr;
 }
