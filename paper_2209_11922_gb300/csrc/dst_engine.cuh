@@ -218,6 +218,16 @@ ETD_PLAN(double, 1536, false, 128, 16, 6, 16)
 template <class L> struct FirstRadix;
 template <int R0, int... Rs> struct FirstRadix<Radices<R0, Rs...>> { static constexpr int value = R0; };
 
+// Twiddle tables: for every pass after the first (NS > 1) the factors w_M^{k r M/(NS R)},
+// k = jj mod NS < NS, r = 1..R-1, are stored r-major at [(r-1)*NS + k], passes back to back, so
+// the lanes of a warp (consecutive jj) read consecutive entries. TwOffset gives a pass's start.
+template <int NS, int... Rs> struct TwSize { static constexpr int value = 0; };
+template <int NS, int R, int... Rest> struct TwSize<NS, R, Rest...> {
+  static constexpr int value = (NS > 1 ? (R - 1) * NS : 0) + TwSize<NS * R, Rest...>::value;
+};
+template <class L> struct TwiddleCount;
+template <int... Rs> struct TwiddleCount<Radices<Rs...>> { static constexpr int value = TwSize<1, Rs...>::value; };
+
 template <class T, int N, bool ODD_> struct PairLayout {
   using Plan = FftPlan<T, N, ODD_>;
   static constexpr bool ODD = Plan::ODD;
@@ -228,16 +238,6 @@ template <class T, int N, bool ODD_> struct PairLayout {
   static constexpr int TWN = TwiddleCount<typename Plan::R>::value;  // twiddle table entries
   static __device__ __forceinline__ int at(int j) { return j + j / PADG; }
 };
-
-// Twiddle tables: for every pass after the first (NS > 1) the factors w_M^{k r M/(NS R)},
-// k = jj mod NS < NS, r = 1..R-1, are stored r-major at [(r-1)*NS + k], passes back to back, so
-// the lanes of a warp (consecutive jj) read consecutive entries. TwOffset gives a pass's start.
-template <int NS, int... Rs> struct TwSize { static constexpr int value = 0; };
-template <int NS, int R, int... Rest> struct TwSize<NS, R, Rest...> {
-  static constexpr int value = (NS > 1 ? (R - 1) * NS : 0) + TwSize<NS * R, Rest...>::value;
-};
-template <class L> struct TwiddleCount;
-template <int... Rs> struct TwiddleCount<Radices<Rs...>> { static constexpr int value = TwSize<1, Rs...>::value; };
 
 // ---------------------------------------------------------------------------------------------
 // Stockham passes over the length-M sequence. Pass with radix R after Ns points are combined:
