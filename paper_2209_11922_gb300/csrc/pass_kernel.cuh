@@ -367,12 +367,12 @@ template <class T, int N, bool ODD> KernelInfo kernel_info() {
 // the per-row tile loads of strided passes (P lanes per row, consecutive rows) on distinct banks.
 inline int pair_stride(const KernelInfo& k, int P) {
   const int groups = 128 / (2 * k.elem);           // complex slots per 128-byte bank cycle
-  const int want = P >= groups ? 1 : groups / P;   // residue modulo `groups`
   int lp = k.lp;
   if (P >= groups) {
-    if (lp % 2 == 0) ++lp;
+    if (lp % 2 == 0) ++lp;                         // odd stride: P lanes of one row on distinct banks
   } else {
-    while (lp % groups != want) ++lp;
+    const int want = (groups / P) % groups;        // residue in [0, groups)
+    lp += ((want - lp % groups) + groups) % groups;  // at most groups - 1 steps, no loop
   }
   return lp;
 }
