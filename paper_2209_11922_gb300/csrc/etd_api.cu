@@ -208,9 +208,23 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   return ETD_OK;
 }
 
+// Pass kernels are launched with programmatic stream serialization (PDL): the next pass may be
+// scheduled while the previous one drains, and waits in-kernel (griddepcontrol.wait) before reading
+// its inputs. ETD_PDL=0 disables it.
 etd_status launch(const Launch& L, cudaStream_t s) {
+  static const int use_pdl = env_int("ETD_PDL", 1);
   void* argv[1] = {const_cast<unsigned char*>(L.args)};
-  cudaError_t e = cudaLaunchKernel(L.fn, L.grid, L.block, argv, L.smem, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = L.grid;
+  cfg.blockDim = L.block;
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = use_pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, L.fn, argv);
   if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return ETD_OK;
 }

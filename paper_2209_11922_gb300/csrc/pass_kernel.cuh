@@ -96,6 +96,12 @@ template <int B> __device__ __forceinline__ void cp_async(void* smem, const void
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Programmatic dependent launch: wait until the previous kernel in the stream has completed and its
+// writes are visible (a no-op when launched without the attribute), and let the next kernel start
+// its prologue early. Every pass waits before its first read of a field.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
@@ -218,11 +224,13 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
     }
   };
 
-  // ---- loads (twiddles of the transformed axis, then the tile)
+  // ---- loads (twiddles of the transformed axis: constant tables, issued before the dependency
+  // wait; then the tile, produced by the previous kernel)
   if (op != OP_PACK && op != OP_UNPACK) {
     const C* gtw = reinterpret_cast<const C*>(A.tw);
     for (int i = tid; i < L::TWN; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
   }
+  griddep_wait();
   if (op == OP_ENTRY || op == OP_PACK) {
     load_dense(A.in0, b0);
   } else {
@@ -332,6 +340,7 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
 
+  griddep_launch_dependents();
   if (op == OP_EXIT) store_dense(b0, A.out0);
   else store_tile(b0, A.out0);
 }
