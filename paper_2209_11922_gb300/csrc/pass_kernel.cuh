@@ -17,6 +17,8 @@
 //   S2        last axis: DST(N2), U~+ = P + tau/c2 phi2(-z) N2~, DST               -> eq. (2.14)
 // with z = tau D (mu_x + mu_y [+ mu_z]) per mode (the tensor H of Section 4 times tau).
 #pragma once
+#include <type_traits>
+
 #include "dst_engine.cuh"
 
 namespace etd {
@@ -151,41 +153,74 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
   }
 
   // ---- tile load / store helpers
-  // issues cp.async copies of one field's tile into buf (complete after cp_async_wait_all)
+  // Tile load of one field into buf. Strided passes: cp.async of one complex pair (two adjacent
+  // x values) per (row j, pair pp); a thread keeps its pair index and walks rows, so no division.
+  // Contiguous passes: 16-byte loads of both rows of a pair staged in registers (all issued before
+  // the first shared store), interleaved into complex slots.
+  constexpr int V = (sizeof(T) == 4 && N % 4 == 0) ? 4 : 2;   // elements per vector load
+  using VL = typename std::conditional<V == 4, float4, VT>::type;
   auto load_tile = [&](const T* __restrict__ src, C* buf) {
     if (contiguous) {
-      for (int idx = tid; idx < P * N; idx += NT) {
-        const int pp = idx / N, j = idx % N;
-        const int q = q0 + pp;
-        C* d = &buf[pp * LP + L::at(j)];
-        if (q < A.npairs) {
-          cp_async<sizeof(T)>(&d->x, src + (size_t)(2 * q) * A.nx + j);
-          cp_async<sizeof(T)>(&d->y, src + (size_t)(2 * q + 1) * A.nx + j);
-        } else {
-          *d = C{T(0), T(0)};
+      constexpr int PER = N / V;                               // vectors per row
+      constexpr int CNT = (PER + TPP - 1) / TPP;               // per thread and row
+      const int q = q0 + p;
+      C* bpp = buf + p * LP;
+      if (q < A.npairs) {
+        const VL* ra = reinterpret_cast<const VL*>(src + (size_t)(2 * q) * A.nx);
+        const VL* rb = reinterpret_cast<const VL*>(src + (size_t)(2 * q + 1) * A.nx);
+        VL va[CNT], vb[CNT];
+#pragma unroll
+        for (int c = 0; c < CNT; ++c) {
+          const int k = l + c * TPP;
+          if (PER % TPP == 0 || k < PER) {
+            va[c] = ra[k];
+            vb[c] = rb[k];
+          }
         }
+#pragma unroll
+        for (int c = 0; c < CNT; ++c) {
+          const int k = l + c * TPP;
+          if (PER % TPP == 0 || k < PER) {
+            const T* a = reinterpret_cast<const T*>(&va[c]);
+            const T* b = reinterpret_cast<const T*>(&vb[c]);
+#pragma unroll
+            for (int e = 0; e < V; ++e) bpp[L::at(V * k + e)] = C{a[e], b[e]};
+          }
+        }
+      } else {
+        for (int j = l; j < N; j += TPP) bpp[L::at(j)] = C{T(0), T(0)};
       }
     } else {
-      for (int idx = tid; idx < P * N; idx += NT) {
-        const int j = idx / P, pp = idx % P;
+      const int pp = tid % P;
+      for (int j = tid / P; j < N; j += NT / P)
         cp_async<2 * sizeof(T)>(&buf[pp * LP + L::at(j)], src + (size_t)base + (size_t)j * stride + 2 * pp);
-      }
     }
   };
   auto store_tile = [&](const C* buf, T* __restrict__ dst) {
     if (contiguous) {
-      for (int idx = tid; idx < P * (N / 2); idx += NT) {
-        const int pp = idx / (N / 2), j2 = idx % (N / 2);
-        const int q = q0 + pp;
-        if (q < A.npairs) {
-          const C c0 = buf[pp * LP + L::at(2 * j2)], c1 = buf[pp * LP + L::at(2 * j2 + 1)];
-          reinterpret_cast<VT*>(dst + (size_t)(2 * q) * A.nx)[j2] = VT{c0.x, c1.x};
-          reinterpret_cast<VT*>(dst + (size_t)(2 * q + 1) * A.nx)[j2] = VT{c0.y, c1.y};
+      constexpr int PER = N / V;
+      const int q = q0 + p;
+      if (q < A.npairs) {
+        const C* bpp = buf + p * LP;
+        VL* ra = reinterpret_cast<VL*>(dst + (size_t)(2 * q) * A.nx);
+        VL* rb = reinterpret_cast<VL*>(dst + (size_t)(2 * q + 1) * A.nx);
+        for (int k = l; k < PER; k += TPP) {
+          VL va, vb;
+          T* a = reinterpret_cast<T*>(&va);
+          T* b = reinterpret_cast<T*>(&vb);
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            const C c = bpp[L::at(V * k + e)];
+            a[e] = c.x;
+            b[e] = c.y;
+          }
+          ra[k] = va;
+          rb[k] = vb;
         }
       }
     } else {
-      for (int idx = tid; idx < P * N; idx += NT) {
-        const int j = idx / P, pp = idx % P;
+      const int pp = tid % P;
+      for (int j = tid / P; j < N; j += NT / P) {
         const C c = buf[pp * LP + L::at(j)];
         reinterpret_cast<VT*>(dst + (size_t)base + (size_t)j * stride)[pp] = VT{c.x, c.y};
       }
