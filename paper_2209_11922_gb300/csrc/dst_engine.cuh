@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace etd {
 
 template <class T> struct Cx { T x, y; };
@@ -77,15 +79,26 @@ __host__ __device__ constexpr double cos96(int m) {
 }
 __host__ __device__ constexpr double sin96(int m) { return cos96((m % 96) + 72); }  // sin t = cos(t - pi/2)
 
-// v * exp(2 pi i m / 96); m is a compile-time constant after unrolling, so the trivial cases fold.
-template <class T> __device__ __forceinline__ Cx<T> twmul96(Cx<T> v, int m) {
-  m %= 96;
-  if (m == 0) return v;
-  if (m == 24) return {-v.y, v.x};
-  if (m == 48) return {-v.x, -v.y};
-  if (m == 72) return {v.y, -v.x};
-  const T c = (T)cos96(m), s = (T)sin96(m);
-  return {c * v.x - s * v.y, c * v.y + s * v.x};
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1.
+template <int B, int E, class F> __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// v * exp(2 pi i M / 96) with M a template constant: the trivial factors are exact and the others
+// are literal constants.
+template <class T, int M> __device__ __forceinline__ Cx<T> twmul96(Cx<T> v) {
+  constexpr int m = M % 96;
+  if constexpr (m == 0) return v;
+  else if constexpr (m == 24) return {-v.y, v.x};
+  else if constexpr (m == 48) return {-v.x, -v.y};
+  else if constexpr (m == 72) return {v.y, -v.x};
+  else {
+    constexpr T c = (T)cos96(m), s = (T)sin96(m);
+    return {c * v.x - s * v.y, c * v.y + s * v.x};
+  }
 }
 
 // In-register DFT of length R with kernel exp(+2 pi i r k / R), natural order in and out.
@@ -131,15 +144,17 @@ __device__ __forceinline__ void Dft<T, R>::run(Cx<T>* x) {
     for (int q = 0; q < Q; ++q) y[s][q] = x[F * q + s];
 #pragma unroll
   for (int s = 0; s < F; ++s) Dft<T, Q>::run(y[s]);
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
     Cx<T> a[F];
-#pragma unroll
-    for (int s = 0; s < F; ++s) a[s] = twmul96(y[s][k], (96 / R) * s * k);
+    static_for<0, F>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      a[s] = twmul96<T, (96 / R) * s * k>(y[s][k]);
+    });
     Dft<T, F>::run(a);
 #pragma unroll
     for (int t = 0; t < F; ++t) x[k + Q * t] = a[t];
-  }
+  });
 }
 
 // Per-(type, N) pass plan: FFT length M, radices of the Stockham passes, threads per pair (TPP).

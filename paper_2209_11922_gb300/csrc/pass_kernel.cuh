@@ -72,20 +72,22 @@ template <class T> __device__ __forceinline__ T phi2_series(T z) {
 }
 
 // phi_1(-zeta), phi_2(-zeta) for zeta >= 0 with E = exp(-zeta): series for zeta < 1, else the
-// recurrence phi_{k+1} = (phi_k - 1/k!)/z, which has no cancellation there.
-template <class T> __device__ __forceinline__ void phi12(T zeta, T E, T& p1, T& p2) {
+// recurrence phi_{k+1} = (phi_k - 1/k!)/z, which has no cancellation there. rz = 1/zeta.
+template <class T> __device__ __forceinline__ void phi12(T zeta, T E, T rz, T& p1, T& p2) {
   if (zeta < T(1)) {
     p2 = phi2_series<T>(-zeta);
     p1 = T(1) - zeta * p2;
   } else {
-    p1 = (T(1) - E) / zeta;
-    p2 = (T(1) - p1) / zeta;
+    p1 = (T(1) - E) * rz;
+    p2 = (T(1) - p1) * rz;
   }
 }
-template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E) {
+template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E, T rz) {
   if (zeta < T(1)) return T(1) - zeta * phi2_series<T>(-zeta);
-  return (T(1) - E) / zeta;
+  return (T(1) - E) * rz;
 }
+// 1/zeta (zeta > 0 where it is used): one division per mode serves every phi of the mode.
+template <class T> __device__ __forceinline__ T recip(T z) { return T(1) / z; }
 
 // Asynchronous global -> shared copies (cp.async): every load of a tile is in flight at once and
 // the CTA waits a single time, instead of one memory latency per register-staged loop iteration.
@@ -331,7 +333,8 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const T zeta = pz[t] + zjj, E = pe[t] * ejj;
-        out[t] = E * uv[t] + tau * phi1_only(zeta, E) * wv[t];
+        const T rz = zeta < T(1) ? T(0) : recip(zeta);
+        out[t] = E * uv[t] + tau * phi1_only(zeta, E, rz) * wv[t];
       }
       b0p[L::at(j)] = C{out[0], out[1]};
       return w;
@@ -344,9 +347,11 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj;
+        const T zc = c2 * zeta;
+        const T rz = zc < T(1) ? (zeta < T(1) ? T(0) : recip(zeta)) : recip(zeta);
         T p1, p2;
-        phi12(zeta, E, p1, p2);
-        const T p1c = phi1_only(c2 * zeta, Ec);
+        phi12(zeta, E, rz, p1, p2);
+        const T p1c = phi1_only(zc, Ec, rz / c2);
         u2[t] = Ec * uv[t] + c2 * tau * p1c * wv[t];
         out[t] = E * uv[t] + tau * (p1 - p2 / c2) * wv[t];
       }
@@ -359,8 +364,9 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const T zeta = pz[t] + zjj, E = pe[t] * ejj;
+      const T rz = zeta < T(1) ? T(0) : recip(zeta);
       T p1, p2;
-      phi12(zeta, E, p1, p2);
+      phi12(zeta, E, rz, p1, p2);
       out[t] = pv[t] + (tau / c2) * p2 * wv[t];
     }
     return C{out[0], out[1]};
