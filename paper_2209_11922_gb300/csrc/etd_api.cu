@@ -185,6 +185,20 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
     a.tiles_x = pl->nx / (2 * P);
     grid = (long long)a.tiles_x * other;
   }
+  // keep the shared memory of a CTA small enough for the CTAs per SM the kernel was built for
+  {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+    const size_t budget = (size_t)optin / (size_t)k->min_blocks - 2048;
+    while (P > 1 && pass_smem_bytes(*k, P, two ? 2 : 1) > budget) {
+      P /= 2;
+      if (axis == 0) grid = (a.npairs + P - 1) / P;
+    }
+    if (axis != 0) {
+      a.tiles_x = pl->nx / (2 * P);
+      grid = (long long)a.tiles_x * ((axis == 1) ? pl->nz : pl->ny);
+    }
+  }
   a.P = P;
   a.lp = pair_stride(*k, P);
   L.fn = k->fn;

@@ -110,8 +110,13 @@ template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
 
+// FP32 kernels whose transforms fit are held to 64 registers (two 512-thread CTAs per SM), so that
+// twice as many warps hide shared-memory and FMA latency; the others keep 128.
+template <class T, int N> constexpr int pass_min_blocks() {
+  return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48)) ? 2 : 1;
+}
 template <class T, int N, bool ODD>
-__global__ void __launch_bounds__(512) pass_kernel(const PassArgs<T> A) {
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(const PassArgs<T> A) {
   using L = PairLayout<T, N, ODD>;
   using C = Cx<T>;
   using VT = typename V2<T>::type;
@@ -398,6 +403,7 @@ struct KernelInfo {
   int padg;     // one padding slot every padg positions
   int twn;      // twiddle table entries
   int radix[4]; // Stockham radices (0-terminated)
+  int min_blocks;  // CTAs per SM the register budget was compiled for
 };
 
 template <int... Rs> void radix_list(int* out, Radices<Rs...>) {
@@ -408,7 +414,7 @@ template <int... Rs> void radix_list(int* out, Radices<Rs...>) {
 template <class T, int N, bool ODD> KernelInfo kernel_info() {
   using L = PairLayout<T, N, ODD>;
   KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
-               ODD ? 1 : 0, L::PADG, L::TWN, {0, 0, 0, 0}};
+               ODD ? 1 : 0, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
   radix_list(k.radix, typename FftPlan<T, N, ODD>::R{});
   return k;
 }
