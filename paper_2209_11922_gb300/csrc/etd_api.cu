@@ -174,9 +174,10 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   } else {
     const int other = (axis == 1) ? pl->nz : pl->ny;
     const int pmin = (sizeof(T) == 4) ? 2 : 1;
+    const int pmax = 64 / (int)sizeof(T);   // 128-byte row segments: wider tiles gained nothing
     P = env_int("ETD_PAIRS_STRIDED", 0);
     if (P <= 0) {
-      P = maxp;
+      P = maxp < pmax ? maxp : pmax;
       while (P > pmin && (pl->nx / (2 * P)) * (long long)other < 2 * pl->num_sms) P /= 2;
     }
     if (P > maxp) P = maxp;
