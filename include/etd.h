@@ -135,6 +135,25 @@ etd_status etd_get_plan_info(etd_plan plan, etd_plan_info* info);
 /* Name of pass kind k (0 <= k < ETD_NUM_PASS_KINDS), or NULL. */
 const char* etd_pass_kind_name(int k);
 
+/* Field monitors without a plan and without allocating (the paper has no counterpart; this serves
+ * callers that cannot allocate GPU memory: code running under a framework that owns every
+ * allocation or a fixed memory budget, real-time loops where an allocation and the synchronisation
+ * it may imply are not allowed, or a health check that must work before any plan exists).
+ * Computes the same mass, energy, max|u| and non-finite count as etd_monitor for the dense device
+ * field u (ndim in {2, 3}, N[a] intervals of size h[a] per axis, diffusion D, dtype) and writes
+ * them to out_dev, a DEVICE pointer to one etd_monitors, asynchronously on `stream`; it does not
+ * synchronise and never returns ETD_ERR_NONFINITE (read out_dev->nonfinite instead).
+ * Scratch: a fixed array inside this library (partial sums of one CTA per 2048 unknowns), present
+ * on every GPU that loads the library until the process exits; at most
+ * ETD_MONITOR_NOALLOC_MAX_UNKNOWNS unknowns, larger fields return ETD_ERR_INVALID_ARG. The first
+ * call on each device looks the scratch address up (cudaGetSymbolAddress): make that first call
+ * before any stream capture on that device. Every call shares the scratch and overwrites all of it
+ * that it reads, so calls whose GPU work overlaps (concurrent streams, several host threads) race;
+ * serialise them. Calls no allocating routine. */
+#define ETD_MONITOR_NOALLOC_MAX_UNKNOWNS 33554432
+etd_status etd_monitor_noalloc(int ndim, const int64_t* N, const double* h, double D, etd_dtype dtype,
+                               const void* u, etd_monitors* out_dev, void* stream);
+
 /* Release the plan's device memory and graphs. NULL is accepted. */
 etd_status etd_destroy(etd_plan plan);
 

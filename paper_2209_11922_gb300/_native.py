@@ -49,6 +49,8 @@ _SIGS = {
     "etd_get_plan_info": (c_int, [c_void_p, ctypes.POINTER(EtdPlanInfo)]),
     "etd_pass_kind_name": (c_char_p, [c_int]),
     "etd_destroy": (c_int, [c_void_p]),
+    "etd_monitor_noalloc": (c_int, [c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), c_double, c_int,
+                                    c_void_p, c_void_p, c_void_p]),
     "etd_status_string": (c_char_p, [c_int]),
     "etd_last_error": (c_char_p, []),
 }

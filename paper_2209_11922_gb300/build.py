@@ -79,6 +79,7 @@ def generate() -> list:
         "}  // namespace etd\n"))
     srcs.append(reg)
     srcs.append(os.path.join(CSRC, "etd_api.cu"))
+    srcs.append(os.path.join(CSRC, "monitor_noalloc.cu"))
     return srcs
 
 

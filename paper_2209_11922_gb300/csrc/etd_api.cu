@@ -33,8 +33,12 @@ const KernelInfo* find_pass_kernel(int elem, int N, int odd);
 using namespace etd;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+void etd_internal_set_error(const char* msg) { g_last_error = msg; }
+
+namespace {
 
 etd_status fail(etd_status s, const char* fmt, ...) {
   char buf[512];

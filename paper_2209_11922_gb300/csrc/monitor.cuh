@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(256) monitor_partial_kernel(const T* __restric
 }
 
 // Reduces `nb` partial records into out[0..3] = mass, energy, maxabs and *bad (one block of 256).
-__global__ void __launch_bounds__(256) monitor_final_kernel(const double* __restrict__ part,
+// Internal linkage: every translation unit that launches it has its own copy.
+static __global__ void __launch_bounds__(256) monitor_final_kernel(const double* __restrict__ part,
                                                             const long long* __restrict__ nonfin, int nb,
                                                             double* __restrict__ out, long long* __restrict__ bad) {
   __shared__ double sh[4][256];
