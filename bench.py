@@ -41,6 +41,29 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _kernel_source_hash() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_2209_11922_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(key: str):
+    """DRAM bytes per launch recorded from an ncu capture, or None if the kernels changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        if t.get("source_hash") != _kernel_source_hash():
+            return None
+        return t["entries"].get(key)
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
 
@@ -217,13 +240,7 @@ def run_gb300(args, w):
     alg_bytes = rw * w.unknowns * esz
     achieved = alg_bytes / (dom_ms * 1e-3 / dom_n) / 1e9
     peak, peak_src = _peaks()
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(f"{w.name}:{dtype}:{dom}")
-        except Exception:
-            traffic = None
+    traffic = _traffic(f"{w.name}:{dtype}:{dom}")
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hbuf = torch.empty(u0.shape, dtype=tdt, pin_memory=True).numpy()
