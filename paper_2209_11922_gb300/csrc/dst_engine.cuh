@@ -260,10 +260,19 @@ template <class T, int N, bool ODD_> struct PairLayout {
 // (jj/Ns)*Ns*R + (jj mod Ns) + r*Ns. In place: all reads, barrier, all writes, barrier.
 // The first pass folds in the input map of the variant (odd extension or the y_j of the
 // recurrence); the last pass of the ODD variant writes only k < N, already scaled by -i sc.
+// Nodal reaction f(u) = flin u + fcub u^3 applied to both packed pencils.
+template <class T> struct React {
+  bool on;
+  T flin, fcub;
+  __device__ __forceinline__ Cx<T> operator()(Cx<T> c) const {
+    return on ? Cx<T>{c.x * (flin + fcub * c.x * c.x), c.y * (flin + fcub * c.y * c.y)} : c;
+  }
+};
+
 template <class T, int N, bool ODD, int NS, bool FIRST, int R, int... Rest>
 __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
-                                         const T* __restrict__ sn, int l, T sc) {
-  // tw points at this pass's table (unused when NS == 1)
+                                         const T* __restrict__ sn, int l, T sc, React<T> rx) {
+  // tw points at this pass's table (unused when NS == 1); the first pass applies rx to its input
   using L = PairLayout<T, N, ODD>;
   constexpr int M = L::M;
   constexpr int TPP = L::TPP;
@@ -283,16 +292,16 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
           if (idx == 0 || idx == N) {
             xv = {T(0), T(0)};
           } else if (idx < N) {
-            xv = bp[L::at(idx)];
+            xv = rx(bp[L::at(idx)]);
           } else {
-            const Cx<T> c = bp[L::at(M - idx)];
+            const Cx<T> c = rx(bp[L::at(M - idx)]);
             xv = {-c.x, -c.y};
           }
         } else if constexpr (FIRST) {
           if (idx == 0) {
             xv = {T(0), T(0)};
           } else {
-            const Cx<T> c = bp[L::at(idx)], d = bp[L::at(N - idx)];
+            const Cx<T> c = rx(bp[L::at(idx)]), d = rx(bp[L::at(N - idx)]);
             const T s = sn[idx];
             xv = s * (c + d) + T(0.5) * (c - d);
           }
@@ -326,12 +335,13 @@ __device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __
     }
   }
   __syncthreads();
-  if constexpr (!LAST) stockham<T, N, ODD, NS * R, false, Rest...>(bp, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc);
+  if constexpr (!LAST) stockham<T, N, ODD, NS * R, false, Rest...>(bp, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc, rx);
 }
 
 template <class T, int N, bool ODD, int... Rs>
-__device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, T sc, Radices<Rs...>) {
-  stockham<T, N, ODD, 1, true, Rs...>(bp, tw, sn, l, sc);
+__device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, T sc, React<T> rx,
+                                        Radices<Rs...>) {
+  stockham<T, N, ODD, 1, true, Rs...>(bp, tw, sn, l, sc, rx);
 }
 
 // `mask` names the lanes of the warp that exist (a CTA may have fewer than 32 threads).
@@ -341,13 +351,15 @@ __device__ __forceinline__ Cx<T> shfl_up_cx(unsigned mask, Cx<T> v, int d, int w
 }
 
 // Full orthonormal DST-I of the pair at bp, in place: on return positions 0..N-1 hold the result
-// (position 0 = 0). sc = sqrt(2/N)/2. tw holds the M-th roots of unity, sn = sin(pi j / N)
+// (position 0 = 0). sc = sqrt(2/N)/2. tw holds the per-pass twiddle tables, sn = sin(pi j / N)
 // (recurrence only). `scr` is shared scratch of TPP/32 complex per pair (recurrence, TPP > 32).
+// With rx.on the input is first mapped through the nodal reaction (fused into the first pass).
 template <class T, int N, bool ODD>
 __device__ __forceinline__ void dst_pair(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
-                                         const T* __restrict__ sn, int l, Cx<T>* scr, T sc) {
+                                         const T* __restrict__ sn, int l, Cx<T>* scr, T sc,
+                                         React<T> rx = React<T>{false, T(0), T(0)}) {
   using L = PairLayout<T, N, ODD>;
-  run_fft<T, N, ODD>(bp, tw, sn, l, sc, typename FftPlan<T, N, ODD>::R{});
+  run_fft<T, N, ODD>(bp, tw, sn, l, sc, rx, typename FftPlan<T, N, ODD>::R{});
   if constexpr (!L::ODD) {
     constexpr int TPP = L::TPP;
     constexpr int C = (N / 2) / TPP;

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   int nd = 0, bsel[3] = {0, 0, 0}, epi[3] = {EPI_PLAIN, EPI_PLAIN, EPI_PLAIN};
   switch (op) {
     case OP_ENTRY: case OP_EXIT: case OP_TRANSFORM: nd = 1; break;
-    case OP_REACT: nd = 2; epi[0] = EPI_REACT; break;
+    case OP_REACT: nd = 2; break;   // the reaction is applied as the second transform reads
     case OP_RK1: nd = 3; bsel[1] = 1; epi[1] = EPI_RK1; break;
     case OP_S1: nd = 3; bsel[1] = 1; epi[1] = EPI_S1; break;
     case OP_S2: nd = 2; epi[0] = EPI_S2; break;
@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   for (int s = 0; s < nd; ++s) {
     const int kind = epi[s];
     C* bp = bsel[s] ? b1p : b0p;
-    dst_pair<T, N, ODD>(bp, tw, sn, l, scrp, A.sc);
+    const React<T> rx{op == OP_REACT && s == 1, flin, fcub};
+    dst_pair<T, N, ODD>(bp, tw, sn, l, scrp, A.sc, rx);
     if (kind != EPI_PLAIN) epilogue_pair<T, N, ODD>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
