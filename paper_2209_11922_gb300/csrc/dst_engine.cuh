@@ -252,6 +252,11 @@ template <class T, int N, bool ODD_> struct PairLayout {
   static constexpr int LP = M + M / PADG + 1;  // minimum complex slots per pair
   static constexpr int TWN = TwiddleCount<typename Plan::R>::value;  // twiddle table entries
   static __device__ __forceinline__ int at(int j) { return j + j / PADG; }
+  // at(j0 + k*TPP) for 0 <= j0 < TPP, linear in k when PADG divides TPP
+  static __device__ __forceinline__ int at_stride(int atj0, int j0, int k) {
+    if constexpr (TPP % PADG == 0) return atj0 + k * (TPP + TPP / PADG);
+    else return at(j0 + k * TPP);
+  }
 };
 
 // ---------------------------------------------------------------------------------------------

@@ -133,6 +133,10 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
   C* b1 = b0 + A.P * LP;
   C* scr = b0 + (two ? 2 : 1) * A.P * LP;
+  // spectral passes (two buffers) also stage the transformed axis's zeta, e, ec tables (3 N values)
+  T* tz = reinterpret_cast<T*>(scr + A.P * (TPP > 32 ? TPP / 32 : 1));
+  T* te = tz + N;
+  T* tcs = te + N;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int P = A.P;
   const int p = tid / TPP, l = tid % TPP;
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   }
 
   // ---- tile load / store helpers
+  const int spp = tid % P, sj0 = tid / P;   // strided tiles: pair and first row of this thread
   // Tile load of one field into buf. Strided passes: cp.async of one complex pair (two adjacent
   // x values) per (row j, pair pp); a thread keeps its pair index and walks rows, so no division.
   // Contiguous passes: 16-byte loads of both rows of a pair staged in registers (all issued before
@@ -198,9 +203,14 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
         for (int j = l; j < N; j += TPP) bpp[L::at(j)] = C{T(0), T(0)};
       }
     } else {
-      const int pp = tid % P;
-      for (int j = tid / P; j < N; j += NT / P)
-        cp_async<2 * sizeof(T)>(&buf[pp * LP + L::at(j)], src + (size_t)base + (size_t)j * stride + 2 * pp);
+      // thread = (pair pp, first row j0); rows j0 + k*TPP, k < N/TPP (N/TPP is exact)
+      C* sd = buf + spp * LP;
+      const T* gs = src + (size_t)base + (size_t)sj0 * stride + 2 * spp;
+      const size_t gstep = (size_t)TPP * stride;
+      const int atj0 = L::at(sj0);
+#pragma unroll
+      for (int k = 0; k < N / TPP; ++k)
+        cp_async<2 * sizeof(T)>(sd + L::at_stride(atj0, sj0, k), gs + k * gstep);
     }
   };
   auto store_tile = [&](const C* buf, T* __restrict__ dst) {
@@ -226,10 +236,14 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
         }
       }
     } else {
-      const int pp = tid % P;
-      for (int j = tid / P; j < N; j += NT / P) {
-        const C c = buf[pp * LP + L::at(j)];
-        reinterpret_cast<VT*>(dst + (size_t)base + (size_t)j * stride)[pp] = VT{c.x, c.y};
+      const C* sd = buf + spp * LP;
+      T* gd = dst + (size_t)base + (size_t)sj0 * stride + 2 * spp;
+      const size_t gstep = (size_t)TPP * stride;
+      const int atj0 = L::at(sj0);
+#pragma unroll
+      for (int k = 0; k < N / TPP; ++k) {
+        const C c = sd[L::at_stride(atj0, sj0, k)];
+        *reinterpret_cast<VT*>(gd + k * gstep) = VT{c.x, c.y};
       }
     }
   };
@@ -240,29 +254,29 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
     const long long dr = (A.ndim == 3 ? (long long)(z - 1) * (A.ny - 1) : 0LL) + (y - 1);
     return dr * (A.nx - 1);
   };
+  // dense rows of this thread's pair (computed once); -1 for boundary rows or pairs past the end
+  long long dra = -1, drb = -1;
+  if (op == OP_ENTRY || op == OP_EXIT || op == OP_PACK || op == OP_UNPACK) {
+    const int q = q0 + p;
+    if (q < A.npairs) {
+      dra = dense_row(2 * q);
+      drb = dense_row(2 * q + 1);
+    }
+  }
   auto load_dense = [&](const T* __restrict__ src, C* buf) {
-    for (int idx = tid; idx < P * N; idx += NT) {
-      const int pp = idx / N, x = idx % N;
-      const int q = q0 + pp;
-      T a = T(0), b = T(0);
-      if (q < A.npairs && x > 0) {
-        const long long ra = dense_row(2 * q), rb = dense_row(2 * q + 1);
-        if (ra >= 0) a = src[ra + x - 1];
-        if (rb >= 0) b = src[rb + x - 1];
-      }
-      buf[pp * LP + L::at(x)] = C{a, b};
+    C* bpp = buf + p * LP;
+    for (int x = l; x < N; x += TPP) {
+      const T a = (x > 0 && dra >= 0) ? src[dra + x - 1] : T(0);
+      const T b = (x > 0 && drb >= 0) ? src[drb + x - 1] : T(0);
+      bpp[L::at(x)] = C{a, b};
     }
   };
   auto store_dense = [&](const C* buf, T* __restrict__ dst) {
-    for (int idx = tid; idx < P * N; idx += NT) {
-      const int pp = idx / N, x = idx % N;
-      const int q = q0 + pp;
-      if (q < A.npairs && x > 0) {
-        const C c = buf[pp * LP + L::at(x)];
-        const long long ra = dense_row(2 * q), rb = dense_row(2 * q + 1);
-        if (ra >= 0) dst[ra + x - 1] = c.x;
-        if (rb >= 0) dst[rb + x - 1] = c.y;
-      }
+    const C* bpp = buf + p * LP;
+    for (int x = l + (l == 0 ? TPP : 0); x < N; x += TPP) {
+      const C c = bpp[L::at(x)];
+      if (dra >= 0) dst[dra + x - 1] = c.x;
+      if (drb >= 0) dst[drb + x - 1] = c.y;
     }
   };
 
@@ -271,6 +285,13 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   if (op != OP_PACK && op != OP_UNPACK) {
     const C* gtw = reinterpret_cast<const C*>(A.tw);
     for (int i = tid; i < L::TWN; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
+  }
+  if (two) {
+    for (int i = tid; i < N; i += NT) {
+      cp_async<sizeof(T)>(&tz[i], &A.zeta[A.axis][i]);
+      cp_async<sizeof(T)>(&te[i], &A.ex[A.axis][i]);
+      cp_async<sizeof(T)>(&tcs[i], &A.ec[A.axis][i]);
+    }
   }
   griddep_wait();
   if (op == OP_ENTRY || op == OP_PACK) {
@@ -294,9 +315,9 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   // ---- per-pencil constants of the spectral epilogues (last axis passes only)
   const int la = A.axis;  // transformed axis
   T pz[2] = {T(0), T(0)}, pe[2] = {T(1), T(1)}, pc[2] = {T(1), T(1)};
-  const T* zj = A.zeta[la];
-  const T* ej = A.ex[la];
-  const T* cj = A.ec[la];
+  const T* zj = tz;   // staged copies of A.zeta[la], A.ex[la], A.ec[la]
+  const T* ej = te;
+  const T* cj = tcs;
   if (op == OP_RK1 || op == OP_S1 || op == OP_S2) {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -440,7 +461,8 @@ inline size_t pass_smem_bytes(const KernelInfo& k, int P, int nbuf) {
   const size_t tw = (size_t)(((k.twn > 0 ? k.twn : 1) + 1) & ~1) * c;
   const size_t bufs = (size_t)nbuf * P * pair_stride(k, P) * c;
   const size_t scr = (size_t)P * (k.tpp > 32 ? k.tpp / 32 : 1) * c;
-  return tw + bufs + scr;
+  const size_t tabs = nbuf == 2 ? 3 * (size_t)k.N * k.elem : 0;   // zeta, e, ec of the spectral passes
+  return tw + bufs + scr + tabs;
 }
 
 }  // namespace etd
