@@ -293,13 +293,96 @@ def run_gb300(args, w):
     return 0
 
 
+def run_batched(args, bw):
+    """Many independent 2D problems advanced by one batch (grouped launches), against the same
+    problems advanced one plan each (the plain GPU solver)."""
+    import torch
+
+    from paper_2209_11922_gb300.etd import Batch, Plan
+
+    world, rank, local = _dist_setup(args)
+    torch.cuda.set_device(local)
+    probs = bw.problems()
+    dtype = args.dtype
+    npdt = np.float32 if dtype == "f32" else np.float64
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    shapes = [(ny - 1, nx - 1) for (nx, ny), _ in probs]
+    sizes = [a * b for a, b in shapes]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    flat0 = torch.empty(int(offs[-1]), dtype=tdt, device="cuda")
+    for i, shp in enumerate(shapes):
+        flat0[int(offs[i]):int(offs[i + 1])] = torch.from_numpy(bw.u0(i, shp).astype(npdt).ravel()).cuda()
+    flat = torch.empty_like(flat0)
+    fields = [flat[int(offs[i]):int(offs[i + 1])].view(shp) for i, shp in enumerate(shapes)]
+    unknowns = int(offs[-1])
+    nsteps = args.time_steps or bw.nsteps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    batch = Batch([p[0] for p in probs], [p[1] for p in probs], bw.tau, 2, dtype, route=args.route)
+    create_s = time.perf_counter() - t0
+    info = batch.info()
+
+    def timed(fn, k):
+        tot = 0.0
+        for _ in range(k):
+            flat.copy_(flat0)
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    timed(lambda: batch.run(fields, nsteps, stream), args.warmup)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: batch.run(fields, nsteps, stream), args.steps)
+    value = unknowns * nsteps * args.steps / (ms * 1e-3)
+    # plain GPU solver: one plan per problem, run one after the other on the same stream
+    plans = [Plan(N, D, bw.tau, 2, dtype, route=args.route) for N, D in probs]
+
+    def run_plans():
+        for pl, f in zip(plans, fields):
+            pl.run(f, nsteps, stream)
+
+    timed(run_plans, 1)
+    ms_plans = timed(run_plans, max(1, args.steps // 2))
+    value_plans = unknowns * nsteps * max(1, args.steps // 2) / (ms_plans * 1e-3)
+    for pl in plans:
+        pl.close()
+    esz = 4 if dtype == "f32" else 8
+    step_bytes = 11 * unknowns * esz
+    achieved = step_bytes / (ms / args.steps / nsteps * 1e-3) / 1e9
+    peak, peak_src = _peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dtype, "data": "synthetic",
+        "config": {"workload": bw.name, "problems": len(probs), "unknowns": unknowns, "time_steps_per_step": nsteps,
+                   "tau": bw.tau, "scheme": "ETDRK2", "launches_per_time_step": info["launches_per_step"],
+                   "tuned_tile_pairs": info["tile_pairs"], "create_s": round(create_s, 3),
+                   "l2": "256 MiB buffer written between bench steps"},
+        "gpu_launches": args.steps * (info["launches_per_step"] * nsteps + 12),
+        "plans_value": value_plans, "speedup_vs_plans": value / value_plans,
+        "roofline": {"bound": "hbm", "kernel": "one time step (all grouped launches)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=inputs.AC2D_1024.name, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default=inputs.AC2D_1024.name,
+                    choices=sorted(inputs.WORKLOADS) + sorted(inputs.BATCH_WORKLOADS))
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--route", default="auto", choices=["auto", "fft", "fft_half"])
     ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time-step count")
@@ -308,6 +391,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload in inputs.BATCH_WORKLOADS:
+        return run_batched(args, inputs.BATCH_WORKLOADS[args.workload])
     w = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

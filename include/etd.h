@@ -157,6 +157,33 @@ etd_status etd_monitor_noalloc(int ndim, const int64_t* N, const double* h, doub
 /* Release the plan's device memory and graphs. NULL is accepted. */
 etd_status etd_destroy(etd_plan plan);
 
+/*
+ * Batches of independent 2D problems (same scheme, tau and options; per problem its own mesh and
+ * D): many EIFE1/EIFE2 solves (eqs. (2.13)/(2.14)) advanced together. Problem i has N[2i], N[2i+1]
+ * intervals of size h[2i], h[2i+1] and diffusion D[i]; the same length rules as etd_plan_create.
+ * Each pass of a time step is one kernel launch per distinct length of the transformed axis,
+ * covering every problem with that length; the tile size of each launch is tuned at creation by
+ * timing the candidates (set ETD_AUTOTUNE=0 to take a fixed choice). Steady-state steps replay as a
+ * CUDA graph. Results equal those of one plan per problem with the same options, bit for bit.
+ * Allocates per-problem fields and tables on the current device. Errors as for etd_plan_create;
+ * count <= 0 is ETD_ERR_INVALID_ARG.
+ */
+typedef struct etd_batch_s* etd_batch;
+etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const double* h, const double* D,
+                            double tau, etd_scheme scheme, const etd_options* opt);
+
+/* Advance every problem by nsteps >= 0 steps: u is a HOST array of `count` DEVICE pointers, u[i] the
+ * dense field of problem i (shape [N[2i+1]-1][N[2i]-1], updated in place). Asynchronous on stream;
+ * the pointer array itself may be reused as soon as the call returns. */
+etd_status etd_batch_run(etd_batch b, void* const* u, int64_t nsteps, void* stream);
+
+/* Total unknowns, launches per time step, and the tuned pencil pairs per tile of the first
+ * max_groups step launches (any pointer may be NULL). */
+etd_status etd_batch_info(etd_batch b, int64_t* unknowns, int* launches_per_step, int* tile_pairs, int max_groups);
+
+/* Release a batch. NULL is accepted. */
+etd_status etd_batch_destroy(etd_batch b);
+
 /* Static description of a status code. */
 const char* etd_status_string(etd_status s);
 

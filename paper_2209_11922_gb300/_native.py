@@ -49,6 +49,11 @@ _SIGS = {
     "etd_get_plan_info": (c_int, [c_void_p, ctypes.POINTER(EtdPlanInfo)]),
     "etd_pass_kind_name": (c_char_p, [c_int]),
     "etd_destroy": (c_int, [c_void_p]),
+    "etd_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double),
+                                 ctypes.POINTER(c_double), c_double, c_int, ctypes.POINTER(EtdOptions)]),
+    "etd_batch_run": (c_int, [c_void_p, ctypes.POINTER(c_void_p), c_int64, c_void_p]),
+    "etd_batch_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int]),
+    "etd_batch_destroy": (c_int, [c_void_p]),
     "etd_monitor_noalloc": (c_int, [c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), c_double, c_int,
                                     c_void_p, c_void_p, c_void_p]),
     "etd_status_string": (c_char_p, [c_int]),

@@ -61,6 +61,7 @@ def generate() -> list:
                     '#include "pass_kernel.cuh"\n'
                     "namespace etd {\n"
                     f"template __global__ void pass_kernel<{tn}, {n}, {o}>(const PassArgs<{tn}>);\n"
+                    f"template __global__ void pass_kernel_batched<{tn}, {n}, {o}>(const PassArgs<{tn}>*, const int2*, {tn}* const*);\n"
                     f"KernelInfo {name}() {{ return kernel_info<{tn}, {n}, {o}>(); }}\n"
                     "}  // namespace etd\n"))
                 srcs.append(path)

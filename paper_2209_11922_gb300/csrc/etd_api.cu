@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -129,6 +130,7 @@ namespace {
 template <class T>
 void fill_common(const etd_plan_s* pl, PassArgs<T>& a) {
   memset(&a, 0, sizeof(a));
+  a.user_slot = -1;
   a.ndim = pl->ndim;
   a.nx = pl->nx;
   a.ny = pl->ny;
@@ -324,75 +326,66 @@ etd_status entry_exit_any(etd_plan_s* pl, bool entry, void* u, std::vector<Launc
   return pl->elem == 4 ? entry_exit<float>(pl, entry, u, out) : entry_exit<double>(pl, entry, u, out);
 }
 
+// FP64 on the host, rounded once to T, appended to h for one axis of length n: the per-pass twiddle
+// tables (pass with NS > 1 and radix R holds exp(2 pi i k r / (NS R)) at [(r-1)*NS + k], k < NS,
+// r = 1..R-1, the layout the Stockham passes read), sin(pi j / n), and per mode i the values
+// zeta = tau D mu_i, exp(-zeta), exp(-c2 zeta) with mu_i = (6/h^2)(1 - cos)/(2 + cos) of theta = i pi / n.
+// offs receives the five table starts (element offsets into h).
+template <class T>
+void append_axis_tables(const KernelInfo* k, int n, double hh, double tauD, double c2, std::vector<T>& h,
+                        size_t offs[5]) {
+  offs[0] = h.size();
+  int NS = 1;
+  size_t t = 0;
+  for (int i = 0; i < 4 && k->radix[i]; ++i) {
+    const int R = k->radix[i];
+    if (NS > 1) {
+      for (int r = 1; r < R; ++r)
+        for (int kk = 0; kk < NS; ++kk, ++t) {
+          const long long num = (long long)kk * r % ((long long)NS * R);
+          const double ang = 2.0 * M_PI * (double)num / (double)(NS * R);
+          h.push_back((T)cos(ang));
+          h.push_back((T)sin(ang));
+        }
+    }
+    NS *= R;
+  }
+  if (t == 0) {
+    h.push_back(T(1));
+    h.push_back(T(0));
+  }
+  offs[1] = h.size();
+  for (int j = 0; j < n; ++j) h.push_back((T)sin(M_PI * (double)j / (double)n));
+  offs[2] = h.size();
+  offs[3] = offs[2] + n;
+  offs[4] = offs[2] + 2 * (size_t)n;
+  h.resize(h.size() + 3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    double zeta = 0.0;
+    if (i > 0) {
+      const double th = M_PI * (double)i / (double)n;
+      const double s = sin(0.5 * th);
+      const double mu = 12.0 / (hh * hh) * s * s / (2.0 + cos(th));  // (6/h^2)(1-cos)/(2+cos)
+      zeta = tauD * mu;
+    }
+    h[offs[2] + i] = (T)zeta;
+    h[offs[3] + i] = (T)exp(-zeta);
+    h[offs[4] + i] = (T)exp(-c2 * zeta);
+  }
+}
+
 template <class T>
 etd_status upload_tables(etd_plan_s* pl) {
-  // FP64 on the host, rounded once to T: per axis tw (2M, M = FFT length), sn, zeta, ex, ec (N each)
-  int fftM[3] = {0, 0, 0};
-  const KernelInfo* kinf[3] = {nullptr, nullptr, nullptr};
-  size_t total = 0;
+  std::vector<T> h;
+  size_t offs[3][5];
   for (int a = 0; a < pl->ndim; ++a) {
     const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a], pl->odd[a]);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %lld", (long long)pl->N[a]);
-    fftM[a] = k->fft_len;
-    kinf[a] = k;
-    total += 2 * (size_t)(k->twn > 0 ? k->twn : 1) + 4 * (size_t)pl->N[a];
+    append_axis_tables<T>(k, (int)pl->N[a], pl->h[a], pl->tau * pl->D, pl->opt.c2, h, offs[a]);
+    pl->sc[a] = 0.5 * sqrt(2.0 / (double)pl->N[a]);
   }
-  std::vector<T> h(total);
-  size_t off = 0;
-  size_t offs[3][5];
-  for (int a = 0; a < pl->ndim; ++a) {
-    const int n = (int)pl->N[a];
-    const double hh = pl->h[a];
-    // per-pass twiddle tables: pass with NS > 1 and radix R holds exp(2 pi i k r / (NS R)) at
-    // [(r-1)*NS + k], k < NS, r = 1..R-1 (the layout the Stockham passes read)
-    offs[a][0] = off;
-    {
-      size_t t = 0;
-      int NS = 1;
-      for (int i = 0; i < 4 && kinf[a]->radix[i]; ++i) {
-        const int R = kinf[a]->radix[i];
-        if (NS > 1) {
-          for (int r = 1; r < R; ++r)
-            for (int k = 0; k < NS; ++k, ++t) {
-              const long long num = (long long)k * r % ((long long)NS * R);
-              const double ang = 2.0 * M_PI * (double)num / (double)(NS * R);
-              h[off + 2 * t] = (T)cos(ang);
-              h[off + 2 * t + 1] = (T)sin(ang);
-            }
-        }
-        NS *= R;
-      }
-      if (t == 0) {
-        h[off] = T(1);
-        h[off + 1] = T(0);
-        t = 1;
-      }
-      off += 2 * t;
-    }
-    (void)fftM;
-    offs[a][1] = off;
-    for (int j = 0; j < n; ++j) h[off + j] = (T)sin(M_PI * (double)j / (double)n);
-    off += n;
-    offs[a][2] = off;
-    offs[a][3] = off + n;
-    offs[a][4] = off + 2 * n;
-    for (int i = 0; i < n; ++i) {
-      double zeta = 0.0;
-      if (i > 0) {
-        const double th = M_PI * (double)i / (double)n;
-        const double s = sin(0.5 * th);
-        const double mu = 12.0 / (hh * hh) * s * s / (2.0 + cos(th));  // (6/h^2)(1-cos)/(2+cos)
-        zeta = pl->tau * pl->D * mu;
-      }
-      h[off + i] = (T)zeta;
-      h[off + n + i] = (T)exp(-zeta);
-      h[off + 2 * n + i] = (T)exp(-pl->opt.c2 * zeta);
-    }
-    off += 3 * (size_t)n;
-    pl->sc[a] = 0.5 * sqrt(2.0 / (double)n);
-  }
-  ETD_CUDA(cudaMalloc(&pl->tables, total * sizeof(T)));
-  ETD_CUDA(cudaMemcpy(pl->tables, h.data(), total * sizeof(T), cudaMemcpyHostToDevice));
+  ETD_CUDA(cudaMalloc(&pl->tables, h.size() * sizeof(T)));
+  ETD_CUDA(cudaMemcpy(pl->tables, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   T* base = static_cast<T*>(pl->tables);
   for (int a = 0; a < pl->ndim; ++a) {
     pl->tw[a] = base + offs[a][0];
@@ -452,6 +445,331 @@ etd_status run_steps(etd_plan_s* pl, int64_t nsteps, cudaStream_t s) {
   for (; done < nsteps; ++done)
     for (const Launch& L : pl->step) {
       etd_status st = launch(L, s);
+      if (st != ETD_OK) return st;
+    }
+  return ETD_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batches of independent 2D problems (uneven meshes and diffusion coefficients, common tau).
+// A pass of the time step is launched once per distinct length of the transformed axis: the launch
+// covers every tile of every problem with that length, each CTA reading its problem's descriptor.
+// The tile size of each launch is picked at creation by timing the candidates on the workspace.
+
+struct BatchGroup {
+  const void* fn = nullptr;     // pass_kernel_batched<T, N, ODD>
+  int axis = 0, op = 0, N = 0, P = 1, nbuf = 1, kind = 0;
+  size_t smem = 0;
+  int nctas = 0, tpp = 1;
+  std::vector<int> inst;        // problems in this group
+  void* d_descs = nullptr;      // PassArgs<T>[inst.size()]
+  void* d_map = nullptr;        // int2[nctas]
+  double alg_bytes = 0;
+};
+
+}  // namespace
+
+struct etd_batch_s {
+  int count = 0, elem = 4, scheme = 2;
+  etd_options opt{};
+  double tau = 0;
+  int device = 0, num_sms = 148, optin = 0;
+  std::vector<int> nx, ny, oddx, oddy;
+  std::vector<double> hx, hy, Dv;
+  std::vector<size_t> field_off;   // element offset of problem i's five fields
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* tables = nullptr;
+  void* d_user = nullptr;          // T*[count], the caller's fields of the current run
+  void* d_aux = nullptr;           // descriptors and tile maps of all groups
+  size_t aux_bytes = 0;
+  std::vector<BatchGroup> step, entry, exit_;
+  int64_t unknowns = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+};
+
+namespace {
+
+struct BatchTables {
+  size_t off[2][5];
+  double sc[2];
+};
+
+// PassArgs of problem i for one op, tile size P; returns the problem's tile count.
+template <class T>
+int batch_args(const etd_batch_s* b, const std::vector<BatchTables>& tabs, int i, int op, int axis, int f_in0,
+               int f_in1, int f_out0, int f_out1, int P, const KernelInfo* k, PassArgs<T>& a) {
+  memset(&a, 0, sizeof(a));
+  a.user_slot = -1;
+  a.ndim = 2;
+  a.nx = b->nx[i];
+  a.ny = b->ny[i];
+  a.nz = 1;
+  const T* base = static_cast<const T*>(b->tables);
+  for (int d = 0; d < 3; ++d) {
+    const int dd = d < 2 ? d : 0;
+    a.zeta[d] = base + tabs[i].off[dd][2];
+    a.ex[d] = base + tabs[i].off[dd][3];
+    a.ec[d] = base + tabs[i].off[dd][4];
+  }
+  a.tw = base + tabs[i].off[axis][0];
+  a.sn = base + tabs[i].off[axis][1];
+  a.sc = (T)tabs[i].sc[axis];
+  a.tau = (T)b->tau;
+  a.c2 = (T)b->opt.c2;
+  a.flin = (T)b->opt.flin;
+  a.fcub = (T)b->opt.fcub;
+  a.op = op;
+  a.axis = axis;
+  T* F = static_cast<T*>(b->ws) + b->field_off[i];
+  const size_t fs = (size_t)b->nx[i] * b->ny[i];
+  auto fld = [&](int f) -> T* { return f < 0 ? nullptr : F + (size_t)f * fs; };
+  a.in0 = fld(f_in0);
+  a.in1 = fld(f_in1);
+  a.out0 = fld(f_out0);
+  a.out1 = fld(f_out1);
+  if (op == OP_ENTRY || op == OP_EXIT) a.user_slot = i;
+  a.P = P;
+  a.lp = pair_stride(*k, P);
+  if (axis == 0) {
+    a.npairs = b->ny[i] / 2;
+    return (a.npairs + P - 1) / P;
+  }
+  a.tiles_x = b->nx[i] / (2 * P);
+  return a.tiles_x;
+}
+
+template <class T>
+etd_status batch_group_upload(etd_batch_s* b, const std::vector<BatchTables>& tabs, BatchGroup& g, int f_in0,
+                              int f_in1, int f_out0, int f_out1, char*& aux_cursor) {
+  const KernelInfo* k = find_pass_kernel((int)sizeof(T), g.N, g.axis == 0 ? b->oddx[g.inst[0]] : b->oddy[g.inst[0]]);
+  std::vector<PassArgs<T>> descs(g.inst.size());
+  std::vector<int2> map;
+  for (size_t li = 0; li < g.inst.size(); ++li) {
+    const int tiles = batch_args<T>(b, tabs, g.inst[li], g.op, g.axis, f_in0, f_in1, f_out0, f_out1, g.P, k, descs[li]);
+    for (int t = 0; t < tiles; ++t) map.push_back(make_int2((int)li, t));
+  }
+  g.nctas = (int)map.size();
+  g.smem = pass_smem_bytes(*k, g.P, g.nbuf);
+  const size_t dbytes = descs.size() * sizeof(PassArgs<T>), mbytes = map.size() * sizeof(int2);
+  g.d_descs = aux_cursor;
+  aux_cursor += (dbytes + 255) & ~(size_t)255;
+  g.d_map = aux_cursor;
+  aux_cursor += (mbytes + 255) & ~(size_t)255;
+  if (aux_cursor > static_cast<char*>(b->d_aux) + b->aux_bytes) return fail(ETD_ERR_CUDA, "batch descriptor area overflow");
+  ETD_CUDA(cudaMemcpy(g.d_descs, descs.data(), dbytes, cudaMemcpyHostToDevice));
+  ETD_CUDA(cudaMemcpy(g.d_map, map.data(), mbytes, cudaMemcpyHostToDevice));
+  return ETD_OK;
+}
+
+etd_status batch_launch(const etd_batch_s* b, const BatchGroup& g, cudaStream_t s) {
+  static const int use_pdl = env_int("ETD_PDL", 1);
+  void* user = b->d_user;
+  void* argv[3] = {const_cast<void**>(&g.d_descs), const_cast<void**>(&g.d_map), &user};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.nctas);
+  cfg.blockDim = dim3((unsigned)(g.P * g.tpp));
+  cfg.dynamicSmemBytes = g.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = use_pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, g.fn, argv);
+  if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batched kernel launch: %s", cudaGetErrorString(e));
+  return ETD_OK;
+}
+
+struct BatchOp {
+  int op, axis, in0, in1, out0, out1, kind, nbuf;
+  double rw;
+};
+
+// Build every group of one op: instances grouped by the length of the transformed axis; the tile
+// size is tuned once per (axis, length, buffers) and reused by later ops with the same shape.
+template <class T>
+etd_status batch_build_op(etd_batch_s* b, const std::vector<BatchTables>& tabs, const BatchOp& o,
+                          std::vector<BatchGroup>& out, char*& aux, std::map<long long, int>& tuned, bool autotune) {
+  std::map<int, std::vector<int>> by_len;
+  for (int i = 0; i < b->count; ++i) by_len[o.axis == 0 ? b->nx[i] : b->ny[i]].push_back(i);
+  for (auto& kv : by_len) {
+    BatchGroup g;
+    g.axis = o.axis;
+    g.op = o.op;
+    g.N = kv.first;
+    g.inst = kv.second;
+    g.nbuf = o.nbuf;
+    g.kind = o.kind;
+    const int odd = o.axis == 0 ? b->oddx[g.inst[0]] : b->oddy[g.inst[0]];
+    const KernelInfo* k = find_pass_kernel((int)sizeof(T), g.N, odd);
+    if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", g.N);
+    g.fn = k->fn_batched;
+    g.tpp = k->tpp;
+    long long unk = 0;
+    for (int i : g.inst) unk += (long long)(b->nx[i] - 1) * (b->ny[i] - 1);
+    g.alg_bytes = o.rw * (double)unk * sizeof(T);
+    {
+      cudaError_t e = cudaFuncSetAttribute(g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b->optin);
+      if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    }
+    // candidate tile sizes: powers of two up to 512 threads, within the shared-memory budget, and
+    // (strided passes) dividing every problem's x extent
+    std::vector<int> cands;
+    const size_t budget = (size_t)b->optin / (size_t)k->min_blocks - 2048;
+    for (int P = 1; P * k->tpp <= 512; P *= 2) {
+      if (pass_smem_bytes(*k, P, o.nbuf) > budget) break;
+      bool ok = true;
+      if (o.axis != 0)
+        for (int i : g.inst) ok = ok && (b->nx[i] % (2 * P) == 0);
+      if (ok) cands.push_back(P);
+    }
+    if (cands.empty()) return fail(ETD_ERR_UNSUPPORTED, "no tile size fits axis length %d", g.N);
+    const long long key = ((long long)o.axis << 40) | ((long long)g.N << 8) | o.nbuf;
+    auto it = tuned.find(key);
+    if (it != tuned.end()) {
+      g.P = it->second;
+    } else if (!autotune || cands.size() == 1) {
+      g.P = cands[cands.size() / 2];
+      tuned[key] = g.P;
+    } else {
+      char* mark = aux;
+      float best = 1e30f;
+      int bestP = cands[0];
+      cudaEvent_t e0, e1;
+      ETD_CUDA(cudaEventCreate(&e0));
+      ETD_CUDA(cudaEventCreate(&e1));
+      for (int P : cands) {
+        g.P = P;
+        aux = mark;
+        etd_status st = batch_group_upload<T>(b, tabs, g, o.in0, o.in1, o.out0, o.out1, aux);
+        if (st != ETD_OK) return st;
+        for (int w = 0; w < 2; ++w)
+          if ((st = batch_launch(b, g, 0)) != ETD_OK) return st;
+        ETD_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 5; ++r)
+          if ((st = batch_launch(b, g, 0)) != ETD_OK) return st;
+        ETD_CUDA(cudaEventRecord(e1, 0));
+        ETD_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          bestP = P;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      aux = mark;
+      g.P = bestP;
+      tuned[key] = bestP;
+    }
+    etd_status st = batch_group_upload<T>(b, tabs, g, o.in0, o.in1, o.out0, o.out1, aux);
+    if (st != ETD_OK) return st;
+    out.push_back(g);
+  }
+  return ETD_OK;
+}
+
+template <class T>
+etd_status batch_build(etd_batch_s* b) {
+  // tables
+  std::vector<T> h;
+  std::vector<BatchTables> tabs(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    const int n[2] = {b->nx[i], b->ny[i]};
+    const double hh[2] = {b->hx[i], b->hy[i]};
+    const int odd[2] = {b->oddx[i], b->oddy[i]};
+    for (int a = 0; a < 2; ++a) {
+      const KernelInfo* k = find_pass_kernel((int)sizeof(T), n[a], odd[a]);
+      if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", n[a]);
+      append_axis_tables<T>(k, n[a], hh[a], b->tau * b->Dv[i], b->opt.c2, h, tabs[i].off[a]);
+      tabs[i].sc[a] = 0.5 * sqrt(2.0 / (double)n[a]);
+    }
+  }
+  ETD_CUDA(cudaMalloc(&b->tables, h.size() * sizeof(T)));
+  ETD_CUDA(cudaMemcpy(b->tables, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  // fields
+  size_t total = 0;
+  b->field_off.resize(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    b->field_off[i] = total;
+    total += 5 * (size_t)b->nx[i] * b->ny[i];
+    total = (total + 63) & ~(size_t)63;   // 256-byte aligned fields
+    b->unknowns += (int64_t)(b->nx[i] - 1) * (b->ny[i] - 1);
+  }
+  b->ws_bytes = total * sizeof(T);
+  cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
+  if (e != cudaSuccess) return fail(ETD_ERR_OOM, "batch workspace of %zu bytes: %s", b->ws_bytes, cudaGetErrorString(e));
+  ETD_CUDA(cudaMemset(b->ws, 0, b->ws_bytes));
+  ETD_CUDA(cudaMalloc(&b->d_user, (size_t)b->count * sizeof(void*)));
+  ETD_CUDA(cudaMemset(b->d_user, 0, (size_t)b->count * sizeof(void*)));
+  // descriptor area: at most (ops) x (problems) descriptors and one map entry per tile at P = 1
+  size_t tiles1 = 0;
+  for (int i = 0; i < b->count; ++i) tiles1 += (size_t)b->ny[i] / 2 + (size_t)b->nx[i] / 2;
+  const int nops = 8;
+  b->aux_bytes = (size_t)nops * ((size_t)b->count * sizeof(PassArgs<T>) + tiles1 * sizeof(int2)) + (size_t)nops * 64 * 512;
+  ETD_CUDA(cudaMalloc(&b->d_aux, b->aux_bytes));
+  char* aux = static_cast<char*>(b->d_aux);
+  enum { V = 0, N0 = 1, V2 = 2, PF = 3, N2 = 4 };
+  std::vector<BatchOp> ops;
+  if (b->scheme == 2) {
+    ops = {{OP_REACT, 0, V, -1, N0, -1, PK_REACT, 1, 2.0},
+           {OP_S1, 1, V, N0, V2, PF, PK_S1, 2, 4.0},
+           {OP_REACT, 0, V2, -1, N2, -1, PK_REACT, 1, 2.0},
+           {OP_S2, 1, N2, PF, V, -1, PK_S2, 2, 3.0}};
+  } else {
+    ops = {{OP_REACT, 0, V, -1, N0, -1, PK_REACT, 1, 2.0}, {OP_RK1, 1, V, N0, V, -1, PK_RK1, 2, 3.0}};
+  }
+  const bool autotune = env_int("ETD_AUTOTUNE", 1) != 0;
+  std::map<long long, int> tuned;
+  for (const BatchOp& o : ops) {
+    etd_status st = batch_build_op<T>(b, tabs, o, b->step, aux, tuned, autotune);
+    if (st != ETD_OK) return st;
+  }
+  const BatchOp ent{OP_ENTRY, 0, -1, -1, V, -1, PK_ENTRY_EXIT, 1, 2.0}, ext{OP_EXIT, 0, V, -1, -1, -1, PK_ENTRY_EXIT, 1, 2.0};
+  etd_status st = batch_build_op<T>(b, tabs, ent, b->entry, aux, tuned, false);
+  if (st != ETD_OK) return st;
+  st = batch_build_op<T>(b, tabs, ext, b->exit_, aux, tuned, false);
+  if (st != ETD_OK) return st;
+  // the autotuner ran passes on the workspace: restore the zero state the boundary slots rely on
+  ETD_CUDA(cudaMemset(b->ws, 0, b->ws_bytes));
+  ETD_CUDA(cudaDeviceSynchronize());
+  return ETD_OK;
+}
+
+etd_status batch_run_steps(etd_batch_s* b, int64_t nsteps, cudaStream_t s) {
+  const int G = env_int("ETD_GRAPH_STEPS", 32);
+  int64_t done = 0;
+  if (G > 0 && nsteps >= G) {
+    if (!b->graph || b->graph_steps != G) {
+      if (b->graph) cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      if (!b->cap_stream) ETD_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      ETD_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+      etd_status st = ETD_OK;
+      for (int k = 0; k < G && st == ETD_OK; ++k)
+        for (const BatchGroup& grp : b->step)
+          if ((st = batch_launch(b, grp, b->cap_stream)) != ETD_OK) break;
+      cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (st != ETD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+      b->graph_steps = G;
+    }
+    for (; done + G <= nsteps; done += G) ETD_CUDA(cudaGraphLaunch(b->graph, s));
+  }
+  for (; done < nsteps; ++done)
+    for (const BatchGroup& grp : b->step) {
+      etd_status st = batch_launch(b, grp, s);
       if (st != ETD_OK) return st;
     }
   return ETD_OK;
@@ -702,6 +1020,102 @@ etd_status etd_destroy(etd_plan pl) {
   if (pl->host_dev) cudaFree(pl->host_dev);
   if (pl->mon_part) cudaFree(pl->mon_part);
   delete pl;
+  return ETD_OK;
+}
+
+etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const double* h, const double* D, double tau,
+                            etd_scheme scheme, const etd_options* opt) {
+  g_last_error.clear();
+  if (!out) return fail(ETD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count <= 0) return fail(ETD_ERR_INVALID_ARG, "count must be positive");
+  if (!N || !h || !D) return fail(ETD_ERR_INVALID_ARG, "N, h or D is NULL");
+  if (scheme != ETD_ETDRK1 && scheme != ETD_ETDRK2) return fail(ETD_ERR_INVALID_ARG, "scheme must be 1 or 2");
+  if (!(std::isfinite(tau) && tau > 0)) return fail(ETD_ERR_INVALID_ARG, "tau must be finite and > 0");
+  etd_options o;
+  etd_options_default(&o);
+  if (opt) o = *opt;
+  if (!(std::isfinite(o.c2) && o.c2 > 0 && o.c2 <= 1)) return fail(ETD_ERR_INVALID_ARG, "c2 must lie in (0, 1]");
+  if (!std::isfinite(o.flin) || !std::isfinite(o.fcub)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
+  if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
+  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF)
+    return fail(ETD_ERR_INVALID_ARG, "unknown route");
+  for (int i = 0; i < count; ++i) {
+    for (int a = 0; a < 2; ++a) {
+      const int64_t n = N[2 * i + a];
+      if (n < 2 || n % 2) return fail(ETD_ERR_INVALID_ARG, "problem %d: N[%d] = %lld must be even and >= 2", i, a, (long long)n);
+      if (!(std::isfinite(h[2 * i + a]) && h[2 * i + a] > 0)) return fail(ETD_ERR_INVALID_ARG, "problem %d: h[%d] must be > 0", i, a);
+      if (!supported_length(n)) return fail(ETD_ERR_UNSUPPORTED, "problem %d: N[%d] = %lld has no kernel", i, a, (long long)n);
+    }
+    if (!(std::isfinite(D[i]) && D[i] > 0)) return fail(ETD_ERR_INVALID_ARG, "problem %d: D must be finite and > 0", i);
+  }
+  etd_batch_s* b = new etd_batch_s();
+  b->count = count;
+  b->scheme = scheme;
+  b->opt = o;
+  b->tau = tau;
+  b->elem = o.dtype == ETD_F32 ? 4 : 8;
+  for (int i = 0; i < count; ++i) {
+    b->nx.push_back((int)N[2 * i]);
+    b->ny.push_back((int)N[2 * i + 1]);
+    b->hx.push_back(h[2 * i]);
+    b->hy.push_back(h[2 * i + 1]);
+    b->Dv.push_back(D[i]);
+    auto odd_of = [&](int64_t n) { return (o.dtype != ETD_F32 || o.route == ETD_ROUTE_FFT_HALF) ? 0 : (o.route == ETD_ROUTE_FFT ? 1 : (n >= 512 ? 1 : 0)); };
+    b->oddx.push_back(odd_of(N[2 * i]));
+    b->oddy.push_back(odd_of(N[2 * i + 1]));
+  }
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    delete b;
+    return fail(ETD_ERR_CUDA, "no CUDA device");
+  }
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  cudaDeviceGetAttribute(&b->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+  etd_status st = b->elem == 4 ? batch_build<float>(b) : batch_build<double>(b);
+  if (st != ETD_OK) {
+    etd_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return ETD_OK;
+}
+
+etd_status etd_batch_run(etd_batch b, void* const* u, int64_t nsteps, void* stream) {
+  if (!b || !u) return fail(ETD_ERR_INVALID_ARG, "batch or u is NULL");
+  if (nsteps < 0) return fail(ETD_ERR_INVALID_ARG, "nsteps < 0");
+  for (int i = 0; i < b->count; ++i)
+    if (!u[i]) return fail(ETD_ERR_INVALID_ARG, "u[%d] is NULL", i);
+  if (nsteps == 0) return ETD_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // pageable source: the copy is staged before the call returns, so u may be reused at once
+  ETD_CUDA(cudaMemcpyAsync(b->d_user, u, (size_t)b->count * sizeof(void*), cudaMemcpyHostToDevice, s));
+  etd_status st;
+  for (const BatchGroup& g : b->entry)
+    if ((st = batch_launch(b, g, s)) != ETD_OK) return st;
+  if ((st = batch_run_steps(b, nsteps, s)) != ETD_OK) return st;
+  for (const BatchGroup& g : b->exit_)
+    if ((st = batch_launch(b, g, s)) != ETD_OK) return st;
+  return ETD_OK;
+}
+
+etd_status etd_batch_info(etd_batch b, int64_t* unknowns, int* launches_per_step, int* tile_pairs, int max_groups) {
+  if (!b) return fail(ETD_ERR_INVALID_ARG, "batch is NULL");
+  if (unknowns) *unknowns = b->unknowns;
+  if (launches_per_step) *launches_per_step = (int)b->step.size();
+  if (tile_pairs)
+    for (int i = 0; i < max_groups && i < (int)b->step.size(); ++i) tile_pairs[i] = b->step[i].P;
+  return ETD_OK;
+}
+
+etd_status etd_batch_destroy(etd_batch b) {
+  if (!b) return ETD_OK;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->ws) cudaFree(b->ws);
+  if (b->tables) cudaFree(b->tables);
+  if (b->d_user) cudaFree(b->d_user);
+  if (b->d_aux) cudaFree(b->d_aux);
+  delete b;
   return ETD_OK;
 }
 

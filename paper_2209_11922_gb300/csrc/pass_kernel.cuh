@@ -44,6 +44,7 @@ template <class T> struct PassArgs {
   int lp;           // complex slots per pair in shared memory (>= the layout minimum)
   int tiles_x;      // strided passes: nx / (2P)
   int npairs;       // contiguous passes: ny * nz / 2
+  int user_slot;    // batched entry/exit passes: index of the caller's field pointer, else -1
   const T* in0;
   const T* in1;
   T* out0;
@@ -116,7 +117,7 @@ template <class T, int N> constexpr int pass_min_blocks() {
   return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48)) ? 2 : 1;
 }
 template <class T, int N, bool ODD>
-__global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(const PassArgs<T> A) {
+__device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) {
   using L = PairLayout<T, N, ODD>;
   using C = Cx<T>;
   using VT = typename V2<T>::type;
@@ -146,11 +147,11 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   int q0 = 0, stride = 0, x0 = 0, o = 0;
   long long base = 0;
   if (contiguous) {
-    q0 = blockIdx.x * P;
+    q0 = tile * P;
   } else {
     const int W = 2 * P;
-    const int xt = blockIdx.x % A.tiles_x;
-    o = blockIdx.x / A.tiles_x;
+    const int xt = tile % A.tiles_x;
+    o = tile / A.tiles_x;
     x0 = xt * W;
     if (A.axis == 1) {
       stride = A.nx;
@@ -413,9 +414,31 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   else store_tile(b0, A.out0);
 }
 
+// One plan: the launch covers the tiles of one field.
+template <class T, int N, bool ODD>
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(const PassArgs<T> A) {
+  pass_body<T, N, ODD>(A, (int)blockIdx.x);
+}
+
+// Batches: one launch covers the tiles of many independent problems whose transformed axis has
+// length N. CTA b works on tile map[b].y of the problem described by descs[map[b].x]; entry and exit
+// passes take the caller's field pointer from user[descs[.].user_slot].
+template <class T, int N, bool ODD>
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
+    pass_kernel_batched(const PassArgs<T>* __restrict__ descs, const int2* __restrict__ map, T* const* __restrict__ user) {
+  const int2 m = map[blockIdx.x];
+  PassArgs<T> A = descs[m.x];
+  if (A.user_slot >= 0) {
+    if (A.op == OP_ENTRY || A.op == OP_PACK) A.in0 = user[A.user_slot];
+    else A.out0 = user[A.user_slot];
+  }
+  pass_body<T, N, ODD>(A, m.y);
+}
+
 // Host-side description of one instantiation.
 struct KernelInfo {
   const void* fn;
+  const void* fn_batched;
   int N;
   int tpp;
   int lp;
@@ -435,7 +458,8 @@ template <int... Rs> void radix_list(int* out, Radices<Rs...>) {
 
 template <class T, int N, bool ODD> KernelInfo kernel_info() {
   using L = PairLayout<T, N, ODD>;
-  KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
+  KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>),
+               reinterpret_cast<const void*>(&pass_kernel_batched<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
                ODD ? 1 : 0, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
   radix_list(k.radix, typename FftPlan<T, N, ODD>::R{});
   return k;

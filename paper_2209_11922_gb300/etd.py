@@ -144,3 +144,72 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many independent 2D problems advanced together (etd_batch_*): per problem its own
+    intervals N_i = (N_x, N_y), mesh sizes (default 1/N) and diffusion D_i; common tau, scheme and
+    options. Fields are a list of CUDA tensors of shape (N_y - 1, N_x - 1)."""
+
+    def __init__(self, N: Sequence[Sequence[int]], D: Sequence[float], tau: float, scheme: int = 2,
+                 dtype: str = "f32", h: Optional[Sequence[Sequence[float]]] = None, c2: float = 0.5,
+                 flin: float = 1.0, fcub: float = -1.0, route: str = "auto"):
+        L = nat.lib()
+        self.N = [tuple(int(v) for v in n) for n in N]
+        self.count = len(self.N)
+        self.h = [tuple(float(v) for v in x) for x in (h if h is not None else [(1.0 / a, 1.0 / b) for a, b in self.N])]
+        self.D = [float(d) for d in D]
+        self.dtype = dtype
+        if len(self.D) != self.count or len(self.h) != self.count:
+            raise ValueError("N, h and D need one entry per problem")
+        opt = nat.EtdOptions()
+        L.etd_options_default(ctypes.byref(opt))
+        opt.dtype, opt.route = _DT[dtype], _ROUTE[route]
+        opt.c2, opt.flin, opt.fcub = float(c2), float(flin), float(fcub)
+        Na = (ctypes.c_int64 * (2 * self.count))(*[v for n in self.N for v in n])
+        ha = (ctypes.c_double * (2 * self.count))(*[v for x in self.h for v in x])
+        Da = (ctypes.c_double * self.count)(*self.D)
+        handle = ctypes.c_void_p()
+        nat.check(L.etd_batch_create(ctypes.byref(handle), self.count, Na, ha, Da, float(tau), int(scheme),
+                                     ctypes.byref(opt)), "etd_batch_create")
+        self._h = handle
+
+    def shapes(self):
+        return [(ny - 1, nx - 1) for nx, ny in self.N]
+
+    def run(self, fields, nsteps: int, stream=None):
+        torch = _torch()
+        tdt = torch.float32 if self.dtype == "f32" else torch.float64
+        if len(fields) != self.count:
+            raise ValueError("one field per problem")
+        for f, shp in zip(fields, self.shapes()):
+            if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == tdt and tuple(f.shape) == shp
+                    and f.is_contiguous()):
+                raise ValueError(f"fields must be contiguous CUDA {tdt} tensors of shapes {self.shapes()[:3]}...")
+        ptrs = (ctypes.c_void_p * self.count)(*[f.data_ptr() for f in fields])
+        nat.check(nat.lib().etd_batch_run(self._h, ptrs, int(nsteps), _stream_ptr(stream)), "etd_batch_run")
+        return fields
+
+    def info(self) -> dict:
+        unk = ctypes.c_int64()
+        nl = ctypes.c_int()
+        tiles = (ctypes.c_int * 64)()
+        nat.check(nat.lib().etd_batch_info(self._h, ctypes.byref(unk), ctypes.byref(nl), tiles, 64), "etd_batch_info")
+        return {"unknowns": unk.value, "launches_per_step": nl.value, "tile_pairs": list(tiles[:min(nl.value, 64)])}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().etd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -88,3 +88,39 @@ AC3D_64 = Workload("allen_cahn_3d_64cubed_D1e-3_tau1e-2_etdrk2", (64, 64, 64), 1
                    -0.9, 0.9, DEFAULT_SEED + 2, ("f32", "f64"))
 
 WORKLOADS = {w.name: w for w in (AC2D_64, AC2D_1024, AC3D_256, AC3D_64)}
+
+
+@dataclass(frozen=True)
+class BatchWorkload:
+    """Many independent 2D Allen-Cahn problems of uneven size: per problem N_x and N_y drawn from
+    `sizes`, D log-uniform in [d_lo, d_hi], u0 uniform(u_lo, u_hi); common tau and step count."""
+
+    name: str
+    count: int
+    sizes: tuple
+    d_lo: float
+    d_hi: float
+    tau: float
+    nsteps: int
+    u_lo: float = -0.9
+    u_hi: float = 0.9
+    seed: int = DEFAULT_SEED + 3
+
+    def problems(self):
+        r = uniform01(self.seed, 3 * self.count)
+        ns = len(self.sizes)
+        out = []
+        for i in range(self.count):
+            nx = self.sizes[min(int(r[3 * i] * ns), ns - 1)]
+            ny = self.sizes[min(int(r[3 * i + 1] * ns), ns - 1)]
+            D = float(np.exp(np.log(self.d_lo) + r[3 * i + 2] * (np.log(self.d_hi) - np.log(self.d_lo))))
+            out.append(((nx, ny), D))
+        return out
+
+    def u0(self, i: int, shape) -> np.ndarray:
+        return uniform_field(shape, self.u_lo, self.u_hi, self.seed + 1000 + i)
+
+
+BATCH_2D_512 = BatchWorkload("batched_2d_512_allen_cahn_N64-384_D1e-4-1e-2_tau1e-2_etdrk2", 512,
+                             (64, 96, 128, 192, 256, 384), 1e-4, 1e-2, 1e-2, 200)
+BATCH_WORKLOADS = {BATCH_2D_512.name: BATCH_2D_512}

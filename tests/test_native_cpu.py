@@ -73,3 +73,19 @@ def test_defaults_and_names(L):
     assert L.etd_status_string(nat.ETD_ERR_NONFINITE) == b"non-finite values"
     assert [L.etd_pass_kind_name(k) for k in range(nat.ETD_NUM_PASS_KINDS)][1] == b"x_react"
     assert L.etd_pass_kind_name(99) is None
+
+
+def test_batch_arguments_rejected_on_the_host(L):
+    p = ctypes.c_void_p()
+    N = (ctypes.c_int64 * 4)(64, 64, 63, 64)
+    h = (ctypes.c_double * 4)(1 / 64, 1 / 64, 1 / 63, 1 / 64)
+    D = (ctypes.c_double * 2)(1e-3, 1e-3)
+    assert L.etd_batch_create(ctypes.byref(p), 0, N, h, D, 0.01, 2, None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_batch_create(ctypes.byref(p), 2, N, h, D, 0.01, 2, None) == nat.ETD_ERR_INVALID_ARG  # odd N
+    N2 = (ctypes.c_int64 * 4)(64, 64, 80, 64)
+    assert L.etd_batch_create(ctypes.byref(p), 2, N2, h, D, 0.01, 2, None) == nat.ETD_ERR_UNSUPPORTED
+    D2 = (ctypes.c_double * 2)(1e-3, -1.0)
+    N3 = (ctypes.c_int64 * 4)(64, 64, 64, 64)
+    assert L.etd_batch_create(ctypes.byref(p), 2, N3, h, D2, 0.01, 2, None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_batch_run(None, None, 1, None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_batch_destroy(None) == nat.ETD_OK
