@@ -164,7 +164,9 @@ etd_status etd_destroy(etd_plan plan);
  * Each pass of a time step is one kernel launch per distinct length of the transformed axis,
  * covering every problem with that length; the tile size of each launch is tuned at creation by
  * timing the candidates (set ETD_AUTOTUNE=0 to take a fixed choice). Steady-state steps replay as a
- * CUDA graph. Results equal those of one plan per problem with the same options, bit for bit.
+ * CUDA graph. Results equal those of one plan per problem with the same options up to rounding
+ * (the batched kernel is a separate instantiation, so the compiler may contract and order the
+ * floating-point operations differently; measured differences are at the dtype's rounding level).
  * Allocates per-problem fields and tables on the current device. Errors as for etd_plan_create;
  * count <= 0 is ETD_ERR_INVALID_ARG.
  */
