@@ -274,79 +274,89 @@ template <class T> struct React {
   }
 };
 
-template <class T, int N, bool ODD, int NS, bool FIRST, int R, int... Rest>
-__device__ __forceinline__ void stockham(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
+template <class T, int N, bool ODD, int NB, int NS, bool FIRST, int R, int... Rest>
+__device__ __forceinline__ void stockham(Cx<T>* const (&bps)[NB], const Cx<T>* __restrict__ tw,
                                          const T* __restrict__ sn, int l, T sc, React<T> rx) {
-  // tw points at this pass's table (unused when NS == 1); the first pass applies rx to its input
+  // tw points at this pass's table (unused when NS == 1); the first pass applies rx to its input.
+  // NB independent pairs (one per buffer) go through the pass together, sharing its barriers.
   using L = PairLayout<T, N, ODD>;
   constexpr int M = L::M;
   constexpr int TPP = L::TPP;
   constexpr int TP = M / R;
   constexpr int QN = (TP + TPP - 1) / TPP;
   constexpr bool LAST = sizeof...(Rest) == 0;
-  Cx<T> v[QN][R];
+  Cx<T> v[NB][QN][R];
 #pragma unroll
-  for (int q = 0; q < QN; ++q) {
-    const int jj = l + TPP * q;
-    if (TP % TPP == 0 || jj < TP) {
+  for (int b = 0; b < NB; ++b) {
+    Cx<T>* __restrict__ bp = bps[b];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int idx = jj + r * TP;
-        Cx<T> xv;
-        if constexpr (FIRST && L::ODD) {
-          if (idx == 0 || idx == N) {
-            xv = {T(0), T(0)};
-          } else if (idx < N) {
-            xv = rx(bp[L::at(idx)]);
+    for (int q = 0; q < QN; ++q) {
+      const int jj = l + TPP * q;
+      if (TP % TPP == 0 || jj < TP) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int idx = jj + r * TP;
+          Cx<T> xv;
+          if constexpr (FIRST && L::ODD) {
+            if (idx == 0 || idx == N) {
+              xv = {T(0), T(0)};
+            } else if (idx < N) {
+              xv = rx(bp[L::at(idx)]);
+            } else {
+              const Cx<T> c = rx(bp[L::at(M - idx)]);
+              xv = {-c.x, -c.y};
+            }
+          } else if constexpr (FIRST) {
+            if (idx == 0) {
+              xv = {T(0), T(0)};
+            } else {
+              const Cx<T> c = rx(bp[L::at(idx)]), d = rx(bp[L::at(N - idx)]);
+              const T s = sn[idx];
+              xv = s * (c + d) + T(0.5) * (c - d);
+            }
           } else {
-            const Cx<T> c = rx(bp[L::at(M - idx)]);
-            xv = {-c.x, -c.y};
+            xv = bp[L::at(idx)];
           }
-        } else if constexpr (FIRST) {
-          if (idx == 0) {
-            xv = {T(0), T(0)};
-          } else {
-            const Cx<T> c = rx(bp[L::at(idx)]), d = rx(bp[L::at(N - idx)]);
-            const T s = sn[idx];
-            xv = s * (c + d) + T(0.5) * (c - d);
+          if (NS > 1 && r > 0) xv = cmul(xv, tw[(r - 1) * NS + (jj % NS)]);
+          v[b][q][r] = xv;
+        }
+        Dft<T, R>::run(v[b][q]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    Cx<T>* __restrict__ bp = bps[b];
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      const int jj = l + TPP * q;
+      if (TP % TPP == 0 || jj < TP) {
+        const int base = (jj / NS) * NS * R + (jj % NS);
+        if constexpr (LAST && L::ODD) {
+          static_assert(R % 2 == 0 && NS * R == M, "last ODD radix must be even");
+#pragma unroll
+          for (int r = 0; r < R / 2; ++r) {   // k = jj + r*NS < N
+            const Cx<T> z = v[b][q][r];
+            const int k = base + r * NS;
+            bp[L::at(k)] = (k == 0) ? Cx<T>{T(0), T(0)} : Cx<T>{sc * z.y, -sc * z.x};
           }
         } else {
-          xv = bp[L::at(idx)];
+#pragma unroll
+          for (int r = 0; r < R; ++r) bp[L::at(base + r * NS)] = v[b][q][r];
         }
-        if (NS > 1 && r > 0) xv = cmul(xv, tw[(r - 1) * NS + (jj % NS)]);
-        v[q][r] = xv;
-      }
-      Dft<T, R>::run(v[q]);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < QN; ++q) {
-    const int jj = l + TPP * q;
-    if (TP % TPP == 0 || jj < TP) {
-      const int base = (jj / NS) * NS * R + (jj % NS);
-      if constexpr (LAST && L::ODD) {
-        static_assert(R % 2 == 0 && NS * R == M, "last ODD radix must be even");
-#pragma unroll
-        for (int r = 0; r < R / 2; ++r) {   // k = jj + r*NS < N
-          const Cx<T> z = v[q][r];
-          const int k = base + r * NS;
-          bp[L::at(k)] = (k == 0) ? Cx<T>{T(0), T(0)} : Cx<T>{sc * z.y, -sc * z.x};
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) bp[L::at(base + r * NS)] = v[q][r];
       }
     }
   }
   __syncthreads();
-  if constexpr (!LAST) stockham<T, N, ODD, NS * R, false, Rest...>(bp, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc, rx);
+  if constexpr (!LAST)
+    stockham<T, N, ODD, NB, NS * R, false, Rest...>(bps, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc, rx);
 }
 
-template <class T, int N, bool ODD, int... Rs>
-__device__ __forceinline__ void run_fft(Cx<T>* bp, const Cx<T>* tw, const T* sn, int l, T sc, React<T> rx,
-                                        Radices<Rs...>) {
-  stockham<T, N, ODD, 1, true, Rs...>(bp, tw, sn, l, sc, rx);
+template <class T, int N, bool ODD, int NB, int... Rs>
+__device__ __forceinline__ void run_fft(Cx<T>* const (&bps)[NB], const Cx<T>* tw, const T* sn, int l, T sc,
+                                        React<T> rx, Radices<Rs...>) {
+  stockham<T, N, ODD, NB, 1, true, Rs...>(bps, tw, sn, l, sc, rx);
 }
 
 // `mask` names the lanes of the warp that exist (a CTA may have fewer than 32 threads).
@@ -355,67 +365,87 @@ __device__ __forceinline__ Cx<T> shfl_up_cx(unsigned mask, Cx<T> v, int d, int w
   return {__shfl_up_sync(mask, v.x, d, width), __shfl_up_sync(mask, v.y, d, width)};
 }
 
-// Full orthonormal DST-I of the pair at bp, in place: on return positions 0..N-1 hold the result
-// (position 0 = 0). sc = sqrt(2/N)/2. tw holds the per-pass twiddle tables, sn = sin(pi j / N)
-// (recurrence only). `scr` is shared scratch of TPP/32 complex per pair (recurrence, TPP > 32).
-// With rx.on the input is first mapped through the nodal reaction (fused into the first pass).
-template <class T, int N, bool ODD>
-__device__ __forceinline__ void dst_pair(Cx<T>* __restrict__ bp, const Cx<T>* __restrict__ tw,
-                                         const T* __restrict__ sn, int l, Cx<T>* scr, T sc,
-                                         React<T> rx = React<T>{false, T(0), T(0)}) {
+// Full orthonormal DST-I of NB independent pairs (one per buffer bps[b]), in place: on return
+// positions 0..N-1 of each hold the result (position 0 = 0). sc = sqrt(2/N)/2. tw holds the
+// per-pass twiddle tables, sn = sin(pi j / N) (recurrence only). scrs[b] is shared scratch of
+// TPP/32 complex per pair (recurrence, TPP > 32). With rx.on the input is first mapped through the
+// nodal reaction (fused into the first pass). Running two transforms together halves the number
+// of barrier-separated phases they cost.
+template <class T, int N, bool ODD, int NB>
+__device__ __forceinline__ void dst_pairs(Cx<T>* const (&bps)[NB], const Cx<T>* __restrict__ tw,
+                                          const T* __restrict__ sn, int l, Cx<T>* const (&scrs)[NB], T sc,
+                                          React<T> rx = React<T>{false, T(0), T(0)}) {
   using L = PairLayout<T, N, ODD>;
-  run_fft<T, N, ODD>(bp, tw, sn, l, sc, rx, typename FftPlan<T, N, ODD>::R{});
+  run_fft<T, N, ODD, NB>(bps, tw, sn, l, sc, rx, typename FftPlan<T, N, ODD>::R{});
   if constexpr (!L::ODD) {
     constexpr int TPP = L::TPP;
     constexpr int C = (N / 2) / TPP;
     static_assert(C * TPP == N / 2, "N/2 must be a multiple of the threads per pair");
-    Cx<T> g[C], e[C];
-#pragma unroll
-    for (int i = 0; i < C; ++i) {
-      const int m = l * C + i;
-      const Cx<T> zm = bp[L::at(m)];
-      if (m == 0) {
-        g[i] = zm;
-        e[i] = {T(0), T(0)};
-      } else {
-        const Cx<T> zn = bp[L::at(N - m)];
-        g[i] = zm + zn;
-        const Cx<T> d = zm - zn;
-        e[i] = {d.y, -d.x};
-      }
-      if (i > 0) g[i] = g[i] + g[i - 1];
-    }
-    // exclusive offset of this lane's chunk within the pair
     constexpr int W = TPP < 32 ? TPP : 32;
-    const Cx<T> tot = g[C - 1];
-    Cx<T> inc = tot;
     const int ls = l % W;
     const unsigned mask = __activemask();  // every thread of the CTA reaches this point converged
+    Cx<T> g[NB][C], e[NB][C], off[NB];
 #pragma unroll
-    for (int d = 1; d < W; d <<= 1) {
-      const Cx<T> t = shfl_up_cx(mask, inc, d, W);
-      if (ls >= d) inc = inc + t;
+    for (int b = 0; b < NB; ++b) {
+      Cx<T>* __restrict__ bp = bps[b];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int m = l * C + i;
+        const Cx<T> zm = bp[L::at(m)];
+        if (m == 0) {
+          g[b][i] = zm;
+          e[b][i] = {T(0), T(0)};
+        } else {
+          const Cx<T> zn = bp[L::at(N - m)];
+          g[b][i] = zm + zn;
+          const Cx<T> d = zm - zn;
+          e[b][i] = {d.y, -d.x};
+        }
+        if (i > 0) g[b][i] = g[b][i] + g[b][i - 1];
+      }
+      // exclusive offset of this lane's chunk within the pair
+      const Cx<T> tot = g[b][C - 1];
+      Cx<T> inc = tot;
+#pragma unroll
+      for (int d = 1; d < W; d <<= 1) {
+        const Cx<T> t = shfl_up_cx(mask, inc, d, W);
+        if (ls >= d) inc = inc + t;
+      }
+      if constexpr (TPP > 32) {
+        if (ls == 31) scrs[b][l / 32] = inc;
+      }
+      off[b] = inc - tot;
     }
+    __syncthreads();
     if constexpr (TPP > 32) {
       constexpr int NW = TPP / 32;
       const int w = l / 32;
-      if (ls == 31) scr[w] = inc;
-      __syncthreads();
 #pragma unroll
-      for (int k = 0; k < NW - 1; ++k)
-        if (k < w) inc = inc + scr[k];
-    } else {
-      __syncthreads();
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int k = 0; k < NW - 1; ++k)
+          if (k < w) off[b] = off[b] + scrs[b][k];
     }
-    const Cx<T> off = inc - tot;
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      const int m = l * C + i;
-      bp[L::at(2 * m)] = (m == 0) ? Cx<T>{T(0), T(0)} : sc * e[i];
-      bp[L::at(2 * m + 1)] = sc * (g[i] + off);
+    for (int b = 0; b < NB; ++b) {
+      Cx<T>* __restrict__ bp = bps[b];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int m = l * C + i;
+        bp[L::at(2 * m)] = (m == 0) ? Cx<T>{T(0), T(0)} : sc * e[b][i];
+        bp[L::at(2 * m + 1)] = sc * (g[b][i] + off[b]);
+      }
     }
     __syncthreads();
   }
+}
+
+template <class T, int N, bool ODD>
+__device__ __forceinline__ void dst_pair(Cx<T>* bp, const Cx<T>* __restrict__ tw, const T* __restrict__ sn, int l,
+                                         Cx<T>* scr, T sc, React<T> rx = React<T>{false, T(0), T(0)}) {
+  Cx<T>* const bps[1] = {bp};
+  Cx<T>* const scrs[1] = {scr};
+  dst_pairs<T, N, ODD, 1>(bps, tw, sn, l, scrs, sc, rx);
 }
 
 // Pointwise epilogue over positions 0..N-1 of one pair: bp[j] = epi(j, bp[j]). The loop is kept

@@ -399,8 +399,22 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     return C{out[0], out[1]};
   };
 
+  // Odd-extension kernels with the full register budget (one CTA of 512 threads per SM) run the
+  // two forward transforms of RK1/S1 (of U and of N0) together, sharing each Stockham pass's
+  // barriers; under the halved budget the second set of butterfly registers would spill.
+  int s0 = 0;
+  if constexpr (L::ODD && pass_min_blocks<T, N>() == 1) {
+    if (op == OP_RK1 || op == OP_S1) {
+      C* const bps[2] = {b0p, b1p};
+      C* const scrs[2] = {scrp, scrp};   // unused by the odd-extension variant
+      dst_pairs<T, N, ODD, 2>(bps, tw, sn, l, scrs, A.sc);
+      epilogue_pair<T, N, ODD>(b1p, l, [&](int j, C w) -> C { return epilogue(epi[1], j, w); });
+      if (op == OP_S1) store_tile(b1, A.out1);
+      s0 = 2;
+    }
+  }
 #pragma unroll 1
-  for (int s = 0; s < nd; ++s) {
+  for (int s = s0; s < nd; ++s) {
     const int kind = epi[s];
     C* bp = bsel[s] ? b1p : b0p;
     const React<T> rx{op == OP_REACT && s == 1, flin, fcub};
