@@ -41,7 +41,10 @@ typedef enum {
   ETD_ERR_UNSUPPORTED = 2,   /* valid request this build cannot run (e.g. an axis length it has no kernel for) */
   ETD_ERR_CUDA = 3,          /* a CUDA runtime call failed; see etd_last_error() */
   ETD_ERR_OOM = 4,           /* device or pinned-host allocation failed */
-  ETD_ERR_NONFINITE = 5      /* etd_monitor found NaN/Inf values in the field */
+  ETD_ERR_NONFINITE = 5,     /* etd_monitor found NaN/Inf values in the field */
+  ETD_ERR_TIMEOUT = 6        /* a tensor-core pass gave up waiting for its own pipeline (a lost
+                                arrival; its CTAs exit instead of hanging) and the field is invalid;
+                                reported by the next synchronising call (etd_run_host, etd_monitor) */
 } etd_status;
 
 typedef enum { ETD_ETDRK1 = 1, ETD_ETDRK2 = 2 } etd_scheme;   /* EIFE1 eq. (2.13), EIFE2 eq. (2.14) */
@@ -52,8 +55,22 @@ typedef enum { ETD_F64 = 0, ETD_F32 = 1 } etd_dtype;            /* arithmetic an
  * ETD_ROUTE_FFT_HALF: a length-N complex FFT per pair of pencils followed by a prefix sum (half the
  *   work; rounding grows like sqrt(N/2) eps).
  * ETD_ROUTE_AUTO: per axis, FP32 takes ETD_ROUTE_FFT for N >= 512 and ETD_ROUTE_FFT_HALF below;
- *   FP64 always takes the recurrence. */
-typedef enum { ETD_ROUTE_AUTO = 0, ETD_ROUTE_FFT = 1, ETD_ROUTE_FFT_HALF = 2 } etd_route;
+ *   FP64 always takes the recurrence.
+ * ETD_ROUTE_GEMM_TF32 and ETD_ROUTE_GEMM_BF16X3 (FP32 plans only; every N[a] a multiple of 32):
+ *   the DST-I along an axis is the dense product with the N x N sine matrix S_a of Section 4,
+ *   computed on the tensor cores with FP32 accumulation and written transposed, so each pass
+ *   contracts a contiguous axis. TF32: the field's values enter the product with TF32 precision
+ *   (10 stored mantissa bits), S_a is rounded to TF32. BF16X3: both operands are split into bf16
+ *   high and low parts and hi*hi + hi*lo + lo*hi are accumulated (about 16 significant bits per
+ *   operand). Errors against the FP64 solution are far above the FFT routes' (see the route's
+ *   documented tolerance); the state between steps is spectral along every axis. */
+typedef enum {
+  ETD_ROUTE_AUTO = 0,
+  ETD_ROUTE_FFT = 1,
+  ETD_ROUTE_FFT_HALF = 2,
+  ETD_ROUTE_GEMM_TF32 = 3,
+  ETD_ROUTE_GEMM_BF16X3 = 4
+} etd_route;
 
 typedef struct {
   etd_dtype dtype;   /* default ETD_F64 */
@@ -74,15 +91,16 @@ etd_status etd_options_default(etd_options* opt);
  * device, and uploads them. Supported N[a]: 2^k (4..2048) and 3*2^k (6..1536).
  * opt may be NULL (defaults). On success *out receives the plan.
  * Errors: ETD_ERR_INVALID_ARG (out/N/h NULL, ndim not 2 or 3, N[a] < 2 or odd, h <= 0, D <= 0,
- * tau <= 0, c2 outside (0, 1], non-finite values), ETD_ERR_UNSUPPORTED (N[a] without a kernel),
- * ETD_ERR_OOM, ETD_ERR_CUDA.
+ * tau <= 0, c2 outside (0, 1], non-finite values, unknown route, a GEMM route with dtype
+ * ETD_F64), ETD_ERR_UNSUPPORTED (N[a] without a kernel; a GEMM route with N[a] not a multiple of
+ * 32), ETD_ERR_OOM, ETD_ERR_CUDA.
  */
 etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const double* h, double D,
                            double tau, etd_scheme scheme, const etd_options* opt);
 
 /* Advance the device field u (in place) by `nsteps` >= 0 time steps on `stream`. nsteps = 0 is a
  * no-op. Equivalent to nsteps calls of etd_step up to rounding (the internal state between steps
- * stays spectral along all axes but the last). Errors: ETD_ERR_INVALID_ARG (plan or u NULL,
+ * stays spectral along all axes but the last, or all axes on the GEMM routes). Errors: ETD_ERR_INVALID_ARG (plan or u NULL,
  * nsteps < 0), ETD_ERR_CUDA. */
 etd_status etd_run(etd_plan plan, void* u, int64_t nsteps, void* stream);
 

@@ -16,9 +16,9 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "etd.h")
 c_int, c_double, c_int64, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                                 ctypes.c_void_p, ctypes.c_char_p)
 
-ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD_ERR_NONFINITE = range(6)
+ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD_ERR_NONFINITE, ETD_ERR_TIMEOUT = range(7)
 ETD_F64, ETD_F32 = 0, 1
-ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF = 0, 1, 2
+ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3 = 0, 1, 2, 3, 4
 ETD_NUM_PASS_KINDS = 8
 
 

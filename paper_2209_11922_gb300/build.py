@@ -81,6 +81,7 @@ def generate() -> list:
     srcs.append(reg)
     srcs.append(os.path.join(CSRC, "etd_api.cu"))
     srcs.append(os.path.join(CSRC, "monitor_noalloc.cu"))
+    srcs.append(os.path.join(CSRC, "gemm_inst.cu"))
     return srcs
 
 

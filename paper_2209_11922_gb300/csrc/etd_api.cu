@@ -10,6 +10,13 @@
 //   3D EIFE1: y T(V->V2) | x REACT(V2->N0) | y T(N0) | z RK1(V,N0 -> V)
 // etd_run enters with x (and y) forward transforms of the dense field and leaves with the inverse
 // ones. Steady-state step lists are captured once into a CUDA graph and replayed.
+//
+// GEMM routes (tensor-core transform passes, gemm_pass.cuh): the state is spectral along every
+// axis; a stage is d inverse passes (the last one applying the reaction) and d forward passes (the
+// last one applying the ETD combination), each pass contracting one axis and rotating the layout:
+//   2D EIFE2: x V->T1 | y REACT T1->T2 | x T2->T1 | y S1(T1,V -> V2,P) | x | y REACT | x | y S2(.,P -> V)
+//   3D: the same with x, y, z passes (six per stage).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,12 +30,15 @@
 #include <vector>
 
 #include "../../include/etd.h"
+#include "gemm_pass.cuh"
 #include "monitor.cuh"
 #include "pass_kernel.cuh"
 
 namespace etd {
 // registry of instantiated pass kernels (generated per (type, N) translation units)
 const KernelInfo* find_pass_kernel(int elem, int N, int odd);
+// tensor-core transform passes (gemm_inst.cu)
+const GemmKernelInfo* find_gemm_kernel(int bn, int route);
 }  // namespace etd
 
 using namespace etd;
@@ -71,7 +81,8 @@ struct Launch {
   dim3 grid, block;
   size_t smem;
   int kind;
-  alignas(16) unsigned char args[sizeof(PassArgs<double>)];
+  alignas(64) unsigned char args[sizeof(PassArgs<double>) > sizeof(GemmParams) ? sizeof(PassArgs<double>)
+                                                                                : sizeof(GemmParams)];
   size_t args_size;
   double alg_bytes;  // algorithmic HBM bytes of this launch (fields read + written)
 };
@@ -123,6 +134,10 @@ struct etd_plan_s {
   double* mon_out = nullptr;
   int mon_blocks = 0;
   size_t ws_bytes = 0;
+  int gemm = 0;               // 0: FFT routes; 1 + GemmRoute: tensor-core transform passes
+  void* gtab = nullptr;       // sine matrices S_a (fp32 TF32-rounded, or bf16 hi and lo)
+  const void* gS[3][2] = {};  // per axis: S (TF32) or S_hi, S_lo (BF16x3)
+  int* dev_err = nullptr;     // set by a tensor-core pass whose wait ran out
 };
 
 namespace {
@@ -322,7 +337,262 @@ etd_status entry_exit(etd_plan_s* pl, bool entry, void* u, std::vector<Launch>& 
   return ETD_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tensor-core transform passes (GEMM routes).
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda).
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a row-major matrix of rows x cols elements of `elem` bytes, tile box {box_cols, box_rows}.
+etd_status make_tmap(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int elem, uint64_t cols, uint64_t rows,
+                     uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swz) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(ETD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (cols * (uint64_t)elem) % 16)
+    return fail(ETD_ERR_UNSUPPORTED, "tensor map: base or row pitch not 16-byte aligned");
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * (cuuint64_t)elem};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ETD_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return ETD_OK;
+}
+
+// Round to TF32 (10 stored mantissa bits), to nearest, ties to even; |v| <= 1 here.
+float round_tf32(double v) {
+  float f = (float)v;
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  b += 0xFFFu + ((b >> 13) & 1u);
+  b &= 0xFFFFE000u;
+  memcpy(&f, &b, 4);
+  return f;
+}
+// Round to bfloat16, to nearest, ties to even; returns the bits and the rounded value.
+uint16_t round_bf16(double v, double* back) {
+  float f = (float)v;
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  const uint16_t h = (uint16_t)(b >> 16);
+  const uint32_t w = (uint32_t)h << 16;
+  float r;
+  memcpy(&r, &w, 4);
+  *back = (double)r;
+  return h;
+}
+
+// S_a[j][k] = sqrt(2/N) sin(pi (j k mod 2N) / N), j, k < N, in FP64, stored per axis in the operand
+// format of the route: fp32 rounded to TF32, or bf16 hi = rn(S), lo = rn(S - hi).
+etd_status upload_gemm_tables(etd_plan_s* pl) {
+  size_t offs[3][2], total = 0;
+  const bool split = pl->gemm - 1 == GR_BF16X3;
+  for (int a = 0; a < pl->ndim; ++a) {
+    const size_t n2 = (size_t)pl->N[a] * pl->N[a];
+    for (int part = 0; part < (split ? 2 : 1); ++part) {
+      offs[a][part] = total;
+      total += ((n2 * (split ? 2 : 4)) + 255) & ~(size_t)255;
+    }
+  }
+  std::vector<unsigned char> h(total, 0);
+  for (int a = 0; a < pl->ndim; ++a) {
+    const long long n = pl->N[a];
+    const double s0 = sqrt(2.0 / (double)n);
+    for (long long j = 0; j < n; ++j)
+      for (long long k = 0; k < n; ++k) {
+        const double v = s0 * sin(M_PI * (double)((j * k) % (2 * n)) / (double)n);
+        const size_t e = (size_t)(j * n + k);
+        if (!split) {
+          const float f = round_tf32(v);
+          memcpy(&h[offs[a][0] + 4 * e], &f, 4);
+        } else {
+          double hv, lv;
+          const uint16_t hb = round_bf16(v, &hv);
+          const uint16_t lb = round_bf16(v - hv, &lv);
+          memcpy(&h[offs[a][0] + 2 * e], &hb, 2);
+          memcpy(&h[offs[a][1] + 2 * e], &lb, 2);
+        }
+      }
+  }
+  ETD_CUDA(cudaMalloc(&pl->gtab, total));
+  ETD_CUDA(cudaMemcpy(pl->gtab, h.data(), total, cudaMemcpyHostToDevice));
+  for (int a = 0; a < pl->ndim; ++a) {
+    pl->gS[a][0] = static_cast<char*>(pl->gtab) + offs[a][0];
+    pl->gS[a][1] = split ? static_cast<char*>(pl->gtab) + offs[a][1] : nullptr;
+  }
+  ETD_CUDA(cudaMalloc(&pl->dev_err, sizeof(int)));
+  ETD_CUDA(cudaMemset(pl->dev_err, 0, sizeof(int)));
+  for (int route = 0; route < 2; ++route)
+    for (int bn = 32; bn <= 256; bn *= 2) {
+      const GemmKernelInfo* k = find_gemm_kernel(bn, route);
+      if (!k) return fail(ETD_ERR_UNSUPPORTED, "no tensor-core pass for tile width %d", bn);
+      ETD_CUDA(cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->smem));
+    }
+  return ETD_OK;
+}
+
+// One tensor-core pass contracting paper axis a of field `in` (pitched, axis a contiguous):
+// out0[k * R + r] = epi((in S_a)[r][k]).
+etd_status make_gemm_launch(etd_plan_s* pl, int a, const void* in, const void* in1, void* out0, void* out1, int op,
+                            int kind, double fields_rw, Launch& L) {
+  const int K = (int)pl->N[a];
+  const int R = (int)(pl->nfield / (size_t)K);
+  const int route = pl->gemm - 1;
+  const int mt = (R + 127) / 128;
+  int bn = env_int("ETD_GEMM_BN", 0);
+  if (bn != 32 && bn != 64 && bn != 128 && bn != 256) {
+    // widest tile that still gives every SM a CTA (wider tiles re-read the field fewer times)
+    bn = 256;
+    while (bn > K) bn /= 2;
+    while (bn > 64 && (long long)mt * ((K + bn - 1) / bn) < pl->num_sms) bn /= 2;
+  }
+  if (bn > K) bn = 32;
+  const GemmKernelInfo* k = find_gemm_kernel(bn, route);
+  if (!k) return fail(ETD_ERR_UNSUPPORTED, "no tensor-core pass for tile width %d", bn);
+  const int nt = (K + bn - 1) / bn;
+  GemmParams prm;
+  memset(&prm, 0, sizeof(prm));
+  etd_status st = make_tmap(&prm.ta, in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)K, (uint64_t)R, 32, 128,
+                            CU_TENSOR_MAP_SWIZZLE_128B);
+  if (st != ETD_OK) return st;
+  if (route == GR_TF32) {
+    st = make_tmap(&prm.tb0, pl->gS[a][0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)K, (uint64_t)K, 32,
+                   (uint32_t)bn, CU_TENSOR_MAP_SWIZZLE_128B);
+  } else {
+    st = make_tmap(&prm.tb0, pl->gS[a][0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)K, (uint64_t)K, 32,
+                   (uint32_t)bn, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (st == ETD_OK)
+      st = make_tmap(&prm.tb1, pl->gS[a][1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)K, (uint64_t)K, 32,
+                     (uint32_t)bn, CU_TENSOR_MAP_SWIZZLE_64B);
+  }
+  if (st != ETD_OK) return st;
+  GemmArgs& g = prm.g;
+  g.op = op;
+  g.R = R;
+  g.K = K;
+  g.row_split = pl->ndim == 3 ? pl->nx : 0;
+  g.in1 = static_cast<const float*>(in1);
+  g.out0 = static_cast<float*>(out0);
+  g.out1 = static_cast<float*>(out1);
+  const int last = pl->ndim - 1;   // spectral passes contract the last axis; rows are (y,) x
+  g.zx = static_cast<const float*>(pl->zeta[0]);
+  g.ex = static_cast<const float*>(pl->ex[0]);
+  g.cx = static_cast<const float*>(pl->ec[0]);
+  g.zy = static_cast<const float*>(pl->zeta[1]);
+  g.ey = static_cast<const float*>(pl->ex[1]);
+  g.cy = static_cast<const float*>(pl->ec[1]);
+  g.zk = static_cast<const float*>(pl->zeta[last]);
+  g.ek = static_cast<const float*>(pl->ex[last]);
+  g.ck = static_cast<const float*>(pl->ec[last]);
+  g.tau = (float)pl->tau;
+  g.c2 = (float)pl->opt.c2;
+  g.flin = (float)pl->opt.flin;
+  g.fcub = (float)pl->opt.fcub;
+  g.err = pl->dev_err;
+  L.fn = k->fn;
+  L.grid = dim3((unsigned)(mt * nt));
+  L.block = dim3((unsigned)k->threads);
+  L.smem = k->smem;
+  L.kind = kind;
+  memcpy(L.args, &prm, sizeof(prm));
+  L.args_size = sizeof(prm);
+  L.alg_bytes = fields_rw * (double)pl->unknowns * 4.0;
+  return ETD_OK;
+}
+
+// Time step of the GEMM routes: per stage d inverse passes (the d-th applies the reaction) and d
+// forward passes (the last applies the ETD combination), alternating between two scratch fields.
+etd_status build_step_gemm(etd_plan_s* pl) {
+  void** F = pl->F;
+  enum { V = 0, T1 = 1, V2 = 2, PF = 3, T2 = 4 };
+  const int d = pl->ndim;
+  pl->step.clear();
+  auto stage = [&](int in, int last_op, int out0, int in1, int out1, int kind_last, double rw_last) -> etd_status {
+    int cur = in;
+    for (int p = 0; p < 2 * d; ++p) {
+      const bool last = p == 2 * d - 1;
+      const int dst = last ? out0 : (p % 2 == 0 ? T1 : T2);
+      const int op = last ? last_op : (p == d - 1 ? GE_REACT : GE_PLAIN);
+      const int kind = last ? kind_last : (p == d - 1 ? PK_REACT : PK_TRANSFORM);
+      Launch L;
+      etd_status st = make_gemm_launch(pl, p % d, F[cur], last ? F[in1] : nullptr, F[dst],
+                                       (last && out1 >= 0) ? F[out1] : nullptr, op, kind, last ? rw_last : 2.0, L);
+      if (st != ETD_OK) return st;
+      pl->step.push_back(L);
+      cur = dst;
+    }
+    return ETD_OK;
+  };
+  etd_status st;
+  if (pl->scheme == 2) {
+    if ((st = stage(V, GE_S1, V2, V, PF, PK_S1, 4.0)) != ETD_OK) return st;
+    if ((st = stage(V2, GE_S2, V, PF, -1, PK_S2, 3.0)) != ETD_OK) return st;
+  } else {
+    if ((st = stage(V, GE_RK1, V, V, -1, PK_RK1, 3.0)) != ETD_OK) return st;
+  }
+  return ETD_OK;
+}
+
+// GEMM routes: entry packs the dense field into V and applies d forward passes (back to the
+// [z][y][x] layout); exit applies d passes into scratch and unpacks.
+etd_status entry_exit_gemm(etd_plan_s* pl, bool entry, void* u, std::vector<Launch>& out) {
+  void** F = pl->F;
+  enum { V = 0, T1 = 1, T2 = 4 };
+  const int d = pl->ndim;
+  Launch L;
+  etd_status st;
+  out.clear();
+  if (entry) {
+    if ((st = make_launch<float>(pl, OP_PACK, 0, u, nullptr, F[V], nullptr, PK_ENTRY_EXIT, 2, L)) != ETD_OK) return st;
+    out.push_back(L);
+  }
+  int cur = V;
+  for (int p = 0; p < d; ++p) {
+    const int dst = (entry && p == d - 1) ? V : (p % 2 == 0 ? T1 : T2);
+    if ((st = make_gemm_launch(pl, p, F[cur], nullptr, F[dst], nullptr, GE_PLAIN, PK_ENTRY_EXIT, 2.0, L)) != ETD_OK)
+      return st;
+    out.push_back(L);
+    cur = dst;
+  }
+  if (!entry) {
+    if ((st = make_launch<float>(pl, OP_UNPACK, 0, F[cur], nullptr, u, nullptr, PK_ENTRY_EXIT, 2, L)) != ETD_OK)
+      return st;
+    out.push_back(L);
+  }
+  return ETD_OK;
+}
+
+// Reads (and clears) the error word of the tensor-core passes; call after synchronising.
+etd_status check_dev_err(etd_plan_s* pl) {
+  if (!pl->dev_err) return ETD_OK;
+  int h = 0;
+  ETD_CUDA(cudaMemcpy(&h, pl->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    ETD_CUDA(cudaMemset(pl->dev_err, 0, sizeof(int)));
+    return fail(ETD_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its pipeline; the field is invalid");
+  }
+  return ETD_OK;
+}
+
 etd_status entry_exit_any(etd_plan_s* pl, bool entry, void* u, std::vector<Launch>& out) {
+  if (pl->gemm) return entry_exit_gemm(pl, entry, u, out);
   return pl->elem == 4 ? entry_exit<float>(pl, entry, u, out) : entry_exit<double>(pl, entry, u, out);
 }
 
@@ -805,8 +1075,11 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   if (!(std::isfinite(o.c2) && o.c2 > 0 && o.c2 <= 1)) return fail(ETD_ERR_INVALID_ARG, "c2 must lie in (0, 1]");
   if (!std::isfinite(o.flin) || !std::isfinite(o.fcub)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
   if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
-  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF)
+  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF &&
+      o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3)
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
+  const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
+  if (gemm && o.dtype != ETD_F32) return fail(ETD_ERR_INVALID_ARG, "the GEMM routes compute in FP32 (dtype ETD_F32)");
   for (int a = 0; a < ndim; ++a) {
     if (N[a] < 2) return fail(ETD_ERR_INVALID_ARG, "N[%d] = %lld < 2", a, (long long)N[a]);
     if (N[a] % 2) return fail(ETD_ERR_INVALID_ARG, "N[%d] = %lld must be even", a, (long long)N[a]);
@@ -816,6 +1089,10 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
     if (!supported_length(N[a]))
       return fail(ETD_ERR_UNSUPPORTED, "N[%d] = %lld: supported lengths are 2^k (4..2048) and 3*2^k (6..1536)", a,
                   (long long)N[a]);
+  if (gemm)
+    for (int a = 0; a < ndim; ++a)
+      if (N[a] % 32)
+        return fail(ETD_ERR_UNSUPPORTED, "N[%d] = %lld: the GEMM routes need multiples of 32", a, (long long)N[a]);
   etd_plan_s* pl = new etd_plan_s();
   pl->ndim = ndim;
   for (int a = 0; a < ndim; ++a) {
@@ -854,7 +1131,13 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   for (int f = 0; f < 5; ++f) pl->F[f] = static_cast<char*>(pl->ws) + f * fbytes;
   etd_status st = (pl->elem == 4) ? upload_tables<float>(pl) : upload_tables<double>(pl);
   if (st != ETD_OK) return bail(st);
-  st = (pl->elem == 4) ? build_step<float>(pl) : build_step<double>(pl);
+  if (gemm) {
+    pl->gemm = 1 + (o.route == ETD_ROUTE_GEMM_TF32 ? GR_TF32 : GR_BF16X3);
+    if ((st = upload_gemm_tables(pl)) != ETD_OK) return bail(st);
+    st = build_step_gemm(pl);
+  } else {
+    st = (pl->elem == 4) ? build_step<float>(pl) : build_step<double>(pl);
+  }
   if (st != ETD_OK) return bail(st);
   pl->mon_blocks = 2 * pl->num_sms;
   e = cudaMalloc(&pl->mon_part, (size_t)pl->mon_blocks * 4 * sizeof(double) + (size_t)pl->mon_blocks * sizeof(long long) +
@@ -899,7 +1182,7 @@ etd_status etd_run_host(etd_plan pl, void* u_host, int64_t nsteps, void* stream)
   if (st != ETD_OK) return st;
   ETD_CUDA(cudaMemcpyAsync(u_host, pl->host_dev, bytes, cudaMemcpyDeviceToHost, s));
   ETD_CUDA(cudaStreamSynchronize(s));
-  return ETD_OK;
+  return check_dev_err(pl);
 }
 
 etd_status etd_apply_dst(etd_plan pl, int axis, const void* in, void* out, void* stream) {
@@ -949,6 +1232,8 @@ etd_status etd_monitor(etd_plan pl, const void* u, etd_monitors* out, void* stre
   long long bad;
   memcpy(&bad, &hbuf[3], sizeof(bad));
   out->nonfinite = bad;
+  etd_status st = check_dev_err(pl);
+  if (st != ETD_OK) return st;
   if (bad) return fail(ETD_ERR_NONFINITE, "%lld non-finite values", bad);
   return ETD_OK;
 }
@@ -1019,6 +1304,8 @@ etd_status etd_destroy(etd_plan pl) {
   if (pl->tables) cudaFree(pl->tables);
   if (pl->host_dev) cudaFree(pl->host_dev);
   if (pl->mon_part) cudaFree(pl->mon_part);
+  if (pl->gtab) cudaFree(pl->gtab);
+  if (pl->dev_err) cudaFree(pl->dev_err);
   delete pl;
   return ETD_OK;
 }
@@ -1038,8 +1325,11 @@ etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const d
   if (!(std::isfinite(o.c2) && o.c2 > 0 && o.c2 <= 1)) return fail(ETD_ERR_INVALID_ARG, "c2 must lie in (0, 1]");
   if (!std::isfinite(o.flin) || !std::isfinite(o.fcub)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
   if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
-  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF)
+  if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF &&
+      o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3)
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
+  const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
+  if (gemm) return fail(ETD_ERR_UNSUPPORTED, "batches run the FFT routes only");
   for (int i = 0; i < count; ++i) {
     for (int a = 0; a < 2; ++a) {
       const int64_t n = N[2 * i + a];
@@ -1127,6 +1417,7 @@ const char* etd_status_string(etd_status s) {
     case ETD_ERR_CUDA: return "CUDA error";
     case ETD_ERR_OOM: return "out of memory";
     case ETD_ERR_NONFINITE: return "non-finite values";
+    case ETD_ERR_TIMEOUT: return "a device wait ran out";
   }
   return "unknown status";
 }

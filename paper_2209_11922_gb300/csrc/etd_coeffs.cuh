@@ -1,0 +1,72 @@
+// etd_coeffs.cuh - per-mode ETD coefficients and launch-ordering helpers shared by the FFT axis
+// passes and the tensor-core transform passes.
+//
+// phi_1, phi_2 of Section 2.2 (phi_0(z) = e^z, phi_{k+1}(z) = (phi_k(z) - 1/k!)/z) evaluated at
+// z = -zeta, zeta = tau * lambda >= 0 of one eigenmode, with E = exp(-zeta) supplied by a table.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace etd {
+
+__host__ __device__ constexpr double inv_factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= (double)k;
+  return 1.0 / f;
+}
+
+// phi_2(z) = sum_{m>=0} z^m / (m+2)! by Horner, for |z| < 1 (truncation below the type's epsilon).
+template <class T> __device__ __forceinline__ T phi2_series(T z) {
+  constexpr int M = sizeof(T) == 4 ? 10 : 18;
+  T p = (T)inv_factorial(M + 1);
+#pragma unroll
+  for (int m = M - 2; m >= 0; --m) p = p * z + (T)inv_factorial(m + 2);
+  return p;
+}
+
+// phi_1(-zeta), phi_2(-zeta) for zeta >= 0 with E = exp(-zeta): series for zeta < 1, else the
+// recurrence phi_{k+1} = (phi_k - 1/k!)/z, which has no cancellation there. rz = 1/zeta.
+template <class T> __device__ __forceinline__ void phi12(T zeta, T E, T rz, T& p1, T& p2) {
+  if (zeta < T(1)) {
+    p2 = phi2_series<T>(-zeta);
+    p1 = T(1) - zeta * p2;
+  } else {
+    p1 = (T(1) - E) * rz;
+    p2 = (T(1) - p1) * rz;
+  }
+}
+template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E, T rz) {
+  if (zeta < T(1)) return T(1) - zeta * phi2_series<T>(-zeta);
+  return (T(1) - E) * rz;
+}
+// 1/zeta (zeta > 0 where it is used): one division per mode serves every phi of the mode.
+template <class T> __device__ __forceinline__ T recip(T z) { return T(1) / z; }
+
+// Correctly rounded reciprocal (the same value as 1/z).
+__device__ __forceinline__ float rcp_rn(float z) { return __frcp_rn(z); }
+__device__ __forceinline__ double rcp_rn(double z) { return __drcp_rn(z); }
+
+// Branch-free forms of phi12 / phi1_only: the series and the closed form are both evaluated and
+// the one valid for zeta selected, so modes on both sides of zeta = 1 in one warp do not diverge
+// and the chains of several modes interleave.
+template <class T> __device__ __forceinline__ void phi12_sel(T zeta, T E, T& p1, T& p2) {
+  const bool small = zeta < T(1);
+  const T s2 = phi2_series<T>(small ? -zeta : T(0));
+  const T rz = rcp_rn(small ? T(1) : zeta);
+  const T c1 = (T(1) - E) * rz;
+  p2 = small ? s2 : (T(1) - c1) * rz;
+  p1 = small ? T(1) - zeta * s2 : c1;
+}
+template <class T> __device__ __forceinline__ T phi1_sel(T zeta, T E) {
+  const bool small = zeta < T(1);
+  const T s2 = phi2_series<T>(small ? -zeta : T(0));
+  const T rz = rcp_rn(small ? T(1) : zeta);
+  return small ? T(1) - zeta * s2 : (T(1) - E) * rz;
+}
+
+// Programmatic dependent launch: wait until the previous kernel in the stream has completed and its
+// writes are visible (a no-op when launched without the attribute), and let the next kernel start
+// its prologue early. Every pass waits before its first read of a field.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+}  // namespace etd

@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "dst_engine.cuh"
+#include "etd_coeffs.cuh"
 
 namespace etd {
 
@@ -57,39 +58,6 @@ template <class T> struct PassArgs {
   T sc, tau, c2, flin, fcub;
 };
 
-__host__ __device__ constexpr double inv_factorial(int n) {
-  double f = 1.0;
-  for (int k = 2; k <= n; ++k) f *= (double)k;
-  return 1.0 / f;
-}
-
-// phi_2(z) = sum_{m>=0} z^m / (m+2)! by Horner, for |z| < 1 (truncation below the type's epsilon).
-template <class T> __device__ __forceinline__ T phi2_series(T z) {
-  constexpr int M = sizeof(T) == 4 ? 10 : 18;
-  T p = (T)inv_factorial(M + 1);
-#pragma unroll
-  for (int m = M - 2; m >= 0; --m) p = p * z + (T)inv_factorial(m + 2);
-  return p;
-}
-
-// phi_1(-zeta), phi_2(-zeta) for zeta >= 0 with E = exp(-zeta): series for zeta < 1, else the
-// recurrence phi_{k+1} = (phi_k - 1/k!)/z, which has no cancellation there. rz = 1/zeta.
-template <class T> __device__ __forceinline__ void phi12(T zeta, T E, T rz, T& p1, T& p2) {
-  if (zeta < T(1)) {
-    p2 = phi2_series<T>(-zeta);
-    p1 = T(1) - zeta * p2;
-  } else {
-    p1 = (T(1) - E) * rz;
-    p2 = (T(1) - p1) * rz;
-  }
-}
-template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E, T rz) {
-  if (zeta < T(1)) return T(1) - zeta * phi2_series<T>(-zeta);
-  return (T(1) - E) * rz;
-}
-// 1/zeta (zeta > 0 where it is used): one division per mode serves every phi of the mode.
-template <class T> __device__ __forceinline__ T recip(T z) { return T(1) / z; }
-
 // Asynchronous global -> shared copies (cp.async): every load of a tile is in flight at once and
 // the CTA waits a single time, instead of one memory latency per register-staged loop iteration.
 template <int B> __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
@@ -100,12 +68,6 @@ template <int B> __device__ __forceinline__ void cp_async(void* smem, const void
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Programmatic dependent launch: wait until the previous kernel in the stream has completed and its
-// writes are visible (a no-op when launched without the attribute), and let the next kernel start
-// its prologue early. Every pass waits before its first read of a field.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };

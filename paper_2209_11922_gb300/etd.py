@@ -13,7 +13,8 @@ import numpy as np
 from . import _native as nat
 
 _DT = {"f64": nat.ETD_F64, "f32": nat.ETD_F32}
-_ROUTE = {"auto": nat.ETD_ROUTE_AUTO, "fft": nat.ETD_ROUTE_FFT, "fft_half": nat.ETD_ROUTE_FFT_HALF}
+_ROUTE = {"auto": nat.ETD_ROUTE_AUTO, "fft": nat.ETD_ROUTE_FFT, "fft_half": nat.ETD_ROUTE_FFT_HALF,
+          "gemm_tf32": nat.ETD_ROUTE_GEMM_TF32, "gemm_bf16x3": nat.ETD_ROUTE_GEMM_BF16X3}
 
 
 def _torch():

@@ -1,0 +1,119 @@
+"""Tensor-core (GEMM) transform routes against the CPU oracle, through the C ABI.
+
+Tolerances come from the operand precision of each route. A transform y = S x with S and x each
+perturbed by a relative representation error u has relative error at most about 2u; the bound
+allowed below is 5 x 2u, with u the route's operand precision:
+  gemm_tf32    TF32 operands keep 10 stored mantissa bits, u = 2^-10 (truncation)   -> 1e-2
+  gemm_bf16x3  x = hi + lo and S = hi + lo in bf16 pairs, u = 2^-16, and the dropped
+               lo*lo product is of the same order                                  -> 1.5e-4
+These runs are short (<= 10 steps), over which diffusion damps rather than amplifies the
+per-transform errors.
+"""
+import numpy as np
+import pytest
+
+from oracle import etd as oetd
+from paper_2209_11922_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROUTES = ("gemm_tf32", "gemm_bf16x3")
+TOL = {"gemm_tf32": 5 * 2 * 2.0 ** -10, "gemm_bf16x3": 1.5e-4}
+
+
+def _plan(N, D, tau, scheme=2, route="gemm_tf32", **kw):
+    from paper_2209_11922_gb300.etd import Plan
+    return Plan(N, D, tau, scheme=scheme, dtype="f32", route=route, **kw)
+
+
+def _rel(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    l2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    linf = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    return l2, linf
+
+
+def _check(got, ref, route, what=""):
+    l2, linf = _rel(got, ref)
+    tol = TOL[route]
+    assert l2 <= tol and linf <= tol, f"{route} {what}: rel L2 {l2:.3e} rel Linf {linf:.3e} (tol {tol:.1e})"
+    return l2, linf
+
+
+def _u0(N, seed, lo=-0.9, hi=0.9):
+    return inputs.uniform_field(inputs.interior_shape(N), lo, hi, seed).astype(np.float32).astype(np.float64)
+
+
+CASES = [
+    # N, D, tau, nsteps, scheme: several 128-row tiles and partial tiles, unequal axes, both schemes
+    ((64, 64), 1e-2, 1e-2, 10, 2),
+    ((64, 96), 1e-2, 1e-2, 5, 2),
+    ((384, 128), 1e-3, 1e-2, 4, 2),
+    ((64, 64), 1e-2, 1e-2, 10, 1),
+    ((64, 64, 64), 1e-3, 1e-2, 3, 2),
+    ((32, 64, 96), 1e-3, 1e-2, 3, 2),
+    ((96, 32, 64), 1e-3, 1e-2, 2, 1),
+]
+
+
+@pytest.mark.parametrize("route", ROUTES)
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])) + f"_s{c[4]}")
+def test_gemm_route_steps_match_oracle(route, case):
+    N, D, tau, nsteps, scheme = case
+    U0 = _u0(N, 31)
+    ref = oetd.run(U0, N, [1.0 / n for n in N], D, tau, nsteps, scheme)
+    with _plan(N, D, tau, scheme, route) as pl:
+        assert pl.info()["kernels_per_step"] == 2 * len(N) * scheme
+        d = torch.from_numpy(U0.astype(np.float32)).cuda()
+        pl.run(d, nsteps)
+        _check(d.cpu().numpy(), ref, route, str(N))
+
+
+@pytest.mark.parametrize("route", ROUTES)
+def test_gemm_route_sine_mode_decays(route):
+    """f = 0: a product sine mode must decay by exp(-n tau D (mu_p + mu_q)) (Section 4)."""
+    N, D, tau, n = (256, 256), 1e-3, 1e-2, 8
+    x = np.arange(1, 256) / 256
+    p, q = 3, 7
+    U0 = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x))
+    mu = lambda k: 6 * 256 ** 2 * (1 - np.cos(k * np.pi / 256)) / (2 + np.cos(k * np.pi / 256))
+    ref = np.exp(-n * tau * D * (mu(p) + mu(q))) * U0
+    with _plan(N, D, tau, 2, route, flin=0.0, fcub=0.0) as pl:
+        d = torch.from_numpy(U0.astype(np.float32)).cuda()
+        pl.run(d, n)
+        _check(d.cpu().numpy(), ref, route, "sine mode")
+
+
+@pytest.mark.parametrize("route", ROUTES)
+def test_gemm_route_run_host_and_monitor(route):
+    N, D, tau = (64, 96), 1e-2, 1e-2
+    U0 = _u0(N, 32).astype(np.float32)
+    with _plan(N, D, tau, 2, route) as pl:
+        d = torch.from_numpy(U0.copy()).cuda()
+        pl.run(d, 4)
+        h = pl.run_host(U0.copy(), 4)
+        assert np.array_equal(h, d.cpu().numpy())
+        assert pl.monitor(d)["status"] == 0
+
+
+@pytest.mark.parametrize("route", ROUTES)
+def test_gemm_route_full_size_3d_256_first_step(route):
+    w = inputs.AC3D_256
+    U0 = w.u0().astype(np.float32).astype(np.float64)
+    ref = oetd.run(U0, w.N, w.h, w.D, w.tau, 1, 2)
+    with _plan(w.N, w.D, w.tau, 2, route) as pl:
+        d = torch.from_numpy(U0.astype(np.float32)).cuda()
+        pl.run(d, 1)
+        _check(d.cpu().numpy(), ref, route, w.name)
+
+
+@pytest.mark.parametrize("route", ROUTES)
+def test_gemm_route_full_size_2d_1024_first_steps(route):
+    w = inputs.AC2D_1024
+    U0 = w.u0().astype(np.float32).astype(np.float64)
+    ref = oetd.run(U0, w.N, w.h, w.D, w.tau, 3, 2)
+    with _plan(w.N, w.D, w.tau, 2, route) as pl:
+        d = torch.from_numpy(U0.astype(np.float32)).cuda()
+        pl.run(d, 3)
+        _check(d.cpu().numpy(), ref, route, w.name)

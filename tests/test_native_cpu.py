@@ -89,3 +89,35 @@ def test_batch_arguments_rejected_on_the_host(L):
     assert L.etd_batch_create(ctypes.byref(p), 2, N3, h, D2, 0.01, 2, None) == nat.ETD_ERR_INVALID_ARG
     assert L.etd_batch_run(None, None, 1, None) == nat.ETD_ERR_INVALID_ARG
     assert L.etd_batch_destroy(None) == nat.ETD_OK
+
+
+def _opts(L, dtype=None, route=None):
+    opt = nat.EtdOptions()
+    L.etd_options_default(ctypes.byref(opt))
+    if dtype is not None:
+        opt.dtype = dtype
+    if route is not None:
+        opt.route = route
+    return opt
+
+
+def test_gemm_route_arguments_rejected_on_the_host(L):
+    for route in (nat.ETD_ROUTE_GEMM_TF32, nat.ETD_ROUTE_GEMM_BF16X3):
+        # FP64 plans have no tensor-core route
+        opt = _opts(L, nat.ETD_F64, route)
+        st, p = _create(L, 2, (64, 64, 1), (1 / 64, 1 / 64, 1.0), opt=ctypes.byref(opt))
+        assert st == nat.ETD_ERR_INVALID_ARG and not p.value
+        # axis lengths must be multiples of 32 (48 has FFT kernels, but no GEMM tiling)
+        opt = _opts(L, nat.ETD_F32, route)
+        st, p = _create(L, 2, (64, 48, 1), (1 / 64, 1 / 48, 1.0), opt=ctypes.byref(opt))
+        assert st == nat.ETD_ERR_UNSUPPORTED and not p.value
+        # batches run the FFT routes only
+        b = ctypes.c_void_p()
+        N = (ctypes.c_int64 * 2)(64, 64)
+        h = (ctypes.c_double * 2)(1 / 64, 1 / 64)
+        D = (ctypes.c_double * 1)(1e-3)
+        assert L.etd_batch_create(ctypes.byref(b), 1, N, h, D, 0.01, 2, ctypes.byref(opt)) == nat.ETD_ERR_UNSUPPORTED
+    opt = _opts(L, nat.ETD_F32, 7)
+    st, _ = _create(L, 2, (64, 64, 1), (1 / 64, 1 / 64, 1.0), opt=ctypes.byref(opt))
+    assert st == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_status_string(nat.ETD_ERR_TIMEOUT) == b"a device wait ran out"
