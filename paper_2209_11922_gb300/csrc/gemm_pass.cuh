@@ -112,7 +112,7 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
       cr *= g.cy[y];
     }
   }
-  const float tau = g.tau, c2 = g.c2, flin = g.flin, fcub = g.fcub;
+  const float tau = g.tau, c2 = g.c2, flin = g.flin, fcub = g.fcub, inv_c2 = 1.f / g.c2;
   const size_t R = (size_t)g.R;
   for (int c0 = cb; c0 < ce; c0 += 16) {
     float v[16];
@@ -141,33 +141,41 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
     const float* tz = tabs + c0;
     const float* te = tabs + BN + c0;
     const float* tc = tabs + 2 * BN + c0;
-    if (op == GE_RK1) {
+    float* o1 = op == GE_S1 ? g.out1 + (size_t)kb * R + r : nullptr;
+    // phi_k(-zeta) in closed form for zeta >= 1 (one reciprocal per mode serves phi_1, phi_2 and
+    // the c2 stage); the series is evaluated only by warps holding a mode that needs it
+    // (zeta < 1, or c2 zeta < 1 in the first stage) - the low-mode corner of the spectrum. Rows
+    // come in whole warps (R is a multiple of 32), so every lane of a warp reaches the votes.
+    const unsigned act = __activemask();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float zeta = zr + tz[j], E = er * te[j];
-        if (j < nv) o0[j * R] = E * w[j] + tau * phi1_sel(zeta, E) * v[j];
+    for (int j = 0; j < 16; ++j) {
+      const float zeta = zr + tz[j], E = er * te[j];
+      const float rz = rcp_rn(fmaxf(zeta, 1.f));
+      float p1 = (1.f - E) * rz, p2 = (1.f - p1) * rz;
+      const bool small = zeta < 1.f;
+      if (__any_sync(act, small)) {
+        const float s2 = phi2_series<float>(small ? -zeta : 0.f);
+        p2 = small ? s2 : p2;
+        p1 = small ? 1.f - zeta * s2 : p1;
       }
-    } else if (op == GE_S1) {
-      float* o1 = g.out1 + (size_t)kb * R + r;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float zeta = zr + tz[j], E = er * te[j], Ec = cr * tc[j];
-        float p1, p2;
-        phi12_sel(zeta, E, p1, p2);
-        const float p1c = phi1_sel(c2 * zeta, Ec);
-        if (j < nv) {
-          o0[j * R] = Ec * w[j] + c2 * tau * p1c * v[j];
-          o1[j * R] = E * w[j] + tau * (p1 - p2 / c2) * v[j];
+      float out;
+      if (op == GE_RK1) {
+        out = E * w[j] + tau * p1 * v[j];
+      } else if (op == GE_S2) {
+        out = w[j] + (tau * inv_c2) * p2 * v[j];
+      } else {
+        const float Ec = cr * tc[j], zc = c2 * zeta;
+        // c2 tau phi1(-c2 zeta) = tau (1 - Ec) / zeta for c2 zeta >= 1
+        float t1 = tau * (1.f - Ec) * rz;
+        if (__any_sync(act, zc < 1.f)) {
+          const bool sm = zc < 1.f;
+          const float s2c = phi2_series<float>(sm ? -zc : 0.f);
+          t1 = sm ? c2 * tau * (1.f - zc * s2c) : t1;
         }
+        out = Ec * w[j] + t1 * v[j];
+        if (j < nv) o1[j * R] = E * w[j] + tau * (p1 - p2 * inv_c2) * v[j];
       }
-    } else {   // GE_S2
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float zeta = zr + tz[j], E = er * te[j];
-        float p1, p2;
-        phi12_sel(zeta, E, p1, p2);
-        if (j < nv) o0[j * R] = w[j] + (tau / c2) * p2 * v[j];
-      }
+      if (j < nv) o0[j * R] = out;
     }
   }
 }
