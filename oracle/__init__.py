@@ -18,6 +18,8 @@ Everything is FP64 NumPy/SciPy, written for readability, not speed:
                eqs. (4.2)-(4.4), with dense per-axis products (tensor mode products of Section 4).
 * ``monitors`` mass 1^T M U, the discrete energy, max|u|.
 * ``transforms`` the orthonormal DST-I of one axis from its definition (kernel-level parity).
+* ``sno``      the spectral neural operator used as the learned coarse propagator (forward pass,
+               its chain-rule gradient, Adam) and the Parareal iteration.
 
 Readings of the paper taken here (each one is listed with its evidence in the design doc):
 
@@ -31,4 +33,4 @@ Readings of the paper taken here (each one is listed with its evidence in DESIGN
 Parity status of each function is stated in its docstring; functions without an independent pin
 say "parity unpinned".
 """
-from . import fem, spectral, phi, etd, monitors, transforms  # noqa: F401
+from . import fem, spectral, phi, etd, monitors, transforms, sno  # noqa: F401

@@ -124,3 +124,54 @@ class BatchWorkload:
 BATCH_2D_512 = BatchWorkload("batched_2d_512_allen_cahn_N64-384_D1e-4-1e-2_tau1e-2_etdrk2", 512,
                              (64, 96, 128, 192, 256, 384), 1e-4, 1e-2, 1e-2, 200)
 BATCH_WORKLOADS = {BATCH_2D_512.name: BATCH_2D_512}
+
+
+@dataclass(frozen=True)
+class SnoWorkload:
+    """Spectral-neural-operator coarse propagator at N x N: C channels, M x M retained sine modes,
+    L layers, predicting `window` ETDRK2 steps of size tau. Training trajectories: u0 uniform(u_lo,
+    u_hi), D log-uniform in [d_lo, d_hi], `traj_steps` steps, input/target pairs every `window`
+    steps. Parareal runs: `batch` problems over `windows` windows."""
+
+    name: str
+    N: int = 256
+    C: int = 32
+    M: int = 24
+    L: int = 4
+    window: int = 50
+    tau: float = 1e-2
+    trajectories: int = 2000
+    traj_steps: int = 200
+    batch: int = 64
+    windows: int = 4
+    d_lo: float = 1e-4
+    d_hi: float = 1e-2
+    u_lo: float = -0.9
+    u_hi: float = 0.9
+    seed: int = DEFAULT_SEED + 5
+
+    def D(self, i: int) -> float:
+        r = float(uniform01(self.seed, 1, offset=i)[0])
+        return float(np.exp(np.log(self.d_lo) + r * (np.log(self.d_hi) - np.log(self.d_lo))))
+
+    def u0(self, i: int) -> np.ndarray:
+        return uniform_field((self.N - 1, self.N - 1), self.u_lo, self.u_hi, self.seed + 7919 * (i + 1))
+
+    def init_weights(self, seed_offset: int = 0) -> dict:
+        """Seeded initial weights: uniform(-s, s) with s = 1 (lift), 1/C (mode mix), 1/sqrt(C)
+        (pointwise), 0.1/sqrt(C) (projection); biases 0."""
+        C, M, L = self.C, self.M, self.L
+        sd = self.seed + 104729 + seed_offset
+        return {
+            "Wl": uniform_field((C, 2), -1.0, 1.0, sd),
+            "bl": np.zeros(C),
+            "Wm": uniform_field((L, M, M, C, C), -1.0 / C, 1.0 / C, sd + 1),
+            "Wp": uniform_field((L, C, C), -1.0 / np.sqrt(C), 1.0 / np.sqrt(C), sd + 2),
+            "bp": np.zeros((L, C)),
+            "Wq": uniform_field((C,), -0.1 / np.sqrt(C), 0.1 / np.sqrt(C), sd + 3),
+            "bq": np.zeros(()),
+        }
+
+
+SNO_256 = SnoWorkload("sno_parareal_2d_256_C32_M24_L4_w50_b64_allen_cahn")
+SNO_WORKLOADS = {SNO_256.name: SNO_256}
