@@ -12,6 +12,7 @@ import re
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libetd_gb300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "etd.h")
+HEADERS = [HEADER, os.path.join(os.path.dirname(HERE), "include", "etd_sno.h")]
 
 c_int, c_double, c_int64, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                                 ctypes.c_void_p, ctypes.c_char_p)
@@ -20,6 +21,10 @@ ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD
 ETD_F64, ETD_F32 = 0, 1
 ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3 = 0, 1, 2, 3, 4
 ETD_NUM_PASS_KINDS = 8
+
+
+class EtdPararealStats(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("fallbacks", c_int), ("correction", c_double * 32)]
 
 
 class EtdOptions(ctypes.Structure):
@@ -56,6 +61,18 @@ _SIGS = {
     "etd_batch_destroy": (c_int, [c_void_p]),
     "etd_monitor_noalloc": (c_int, [c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), c_double, c_int,
                                     c_void_p, c_void_p, c_void_p]),
+    "etd_sno_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int]),
+    "etd_sno_param_count": (c_int64, [c_void_p]),
+    "etd_sno_set_params": (c_int, [c_void_p, c_void_p]),
+    "etd_sno_get_params": (c_int, [c_void_p, c_void_p]),
+    "etd_sno_forward": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_double), c_int, c_void_p, c_void_p]),
+    "etd_sno_train_step": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_double), c_void_p, c_int, ctypes.c_float,
+                                   ctypes.POINTER(c_double), c_void_p, c_void_p]),
+    "etd_sno_destroy": (c_int, [c_void_p]),
+    "etd_parareal_create": (c_int, [ctypes.POINTER(c_void_p), c_void_p, c_int, c_int, ctypes.POINTER(c_double),
+                                    c_double, c_int, c_int]),
+    "etd_parareal_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_void_p, c_void_p]),
+    "etd_parareal_destroy": (c_int, [c_void_p]),
     "etd_status_string": (c_char_p, [c_int]),
     "etd_last_error": (c_char_p, []),
 }
@@ -64,8 +81,8 @@ _lib = None
 
 
 def header_functions() -> list:
-    """Names of the functions declared in include/etd.h."""
-    text = open(HEADER).read()
+    """Names of the functions declared in include/etd.h and include/etd_sno.h."""
+    text = "\n".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(etd_[a-z_0-9]+)\s*\(",
                                  text, flags=re.M)))

@@ -82,13 +82,14 @@ def generate() -> list:
     srcs.append(os.path.join(CSRC, "etd_api.cu"))
     srcs.append(os.path.join(CSRC, "monitor_noalloc.cu"))
     srcs.append(os.path.join(CSRC, "gemm_inst.cu"))
+    srcs.append(os.path.join(CSRC, "sno.cu"))
     return srcs
 
 
 def _compile(src: str) -> tuple:
     obj = os.path.join(BUILD, "obj", os.path.basename(src).replace(".cu", ".o"))
     os.makedirs(os.path.dirname(obj), exist_ok=True)
-    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "etd.h")]
+    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "etd.h"), os.path.join(INCLUDE, "etd_sno.h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj, ""
     cmd = [nvcc(), *_flags(), "-c", src, "-o", obj]

@@ -1,0 +1,255 @@
+// sno_kernels.cuh - kernels of the spectral neural operator (the learned coarse propagator of the
+// Parareal loop) and its training: a strided batched FP32 GEMM with fused epilogues, elementwise
+// maps (lift, GELU gradient, loss gradient), batch reductions and the Adam update.
+//
+// Operator (per field of an N x N mesh, n = N - 1 interior nodes per axis, C channels, M x M
+// retained sine modes S_M[p][j] = sqrt(2/N) sin((p+1)(j+1) pi / N), L layers):
+//   h_0 = lift(u, a);  per layer: hh = bf(S_M h S_M^T); gh[o] = sum_c bf(Wm[p,q,o,c]) hh[c];
+//   z = S_M^T gh S_M + Wp h + bp;  h' = gelu(z);   u_hat = u + Wq . h_L + bq,
+// with bf = round to bfloat16 and a = (ln D - ln 1e-3) / ln 100.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace etd {
+namespace sno {
+
+// round-to-nearest-even to bfloat16, kept in an fp32 register
+__device__ __forceinline__ float bf16_round(float x) {
+  uint32_t b = __float_as_uint(x);
+  b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+  return __uint_as_float(b);
+}
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+enum GemmEpiKind : int {
+  SG_NONE = 0,        // C = alpha acc + beta C
+  SG_BIAS = 1,        // ... + bias[i]
+  SG_BIAS_GELU = 2,   // ... + bias[i] -> C, gelu of it -> C2
+  SG_RESID = 3,       // ... + R[b][i][j] (+ bias[i] when bias is given)
+};
+
+// C[b][i][j] = alpha sum_k A[b][i][k] B[b][k][j] (+ beta C) (+ epilogue), every operand addressed
+// by (row, column, batch) element strides, so transposes and broadcasts are strides.
+struct SGemm {
+  int M, N, K, batch;
+  const float* A; long long a_rs, a_cs, a_bs;
+  const float* B; long long b_rs, b_cs, b_bs;
+  float* C; long long c_rs, c_cs, c_bs;
+  float alpha, beta;
+  int round_a, round_b, round_c;   // bf16 rounding of A, B on load, of the result on store
+  int epi;
+  const float* bias;               // [M] (SG_BIAS, SG_BIAS_GELU)
+  float* C2;                       // gelu(C) with C's strides (SG_BIAS_GELU)
+  const float* R;                  // with C's strides (SG_RESID; bias[i] is added too when given)
+  int ksplit;                      // >1: blockIdx.z = batch * ksplit + s sums K range s into C + s * c_ss
+  long long c_ss;
+};
+
+constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
+
+// 256 threads, 4 x 4 outputs each; tiles staged in shared memory. A operand loads walk the
+// contiguous index of A (K when a_cs == 1, rows otherwise), same for B.
+__global__ void __launch_bounds__(256) sgemm_kernel(const SGemm g) {
+  __shared__ float As[SG_BK][SG_BM + 4];
+  __shared__ float Bs[SG_BK][SG_BN + 4];
+  const int ks = g.ksplit > 1 ? g.ksplit : 1;
+  const int bz = blockIdx.z / ks, sk = blockIdx.z % ks;
+  const int kc = ((g.K + ks - 1) / ks + SG_BK - 1) / SG_BK * SG_BK;   // K range of this split
+  const int kbeg = sk * kc, kend = min(g.K, kbeg + kc);
+  const int i0 = blockIdx.y * SG_BM, j0 = blockIdx.x * SG_BN;
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const float* A = g.A + bz * g.a_bs;
+  const float* B = g.B + bz * g.b_bs;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  const bool a_kfast = g.a_cs == 1 || g.a_rs != 1;
+  const bool b_jfast = g.b_cs == 1 || g.b_rs != 1;
+  for (int k0 = kbeg; k0 < kend; k0 += SG_BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = t + 256 * r;   // 0..1023 over the 64 x 16 tile
+      int ii, kk;
+      if (a_kfast) { ii = e / SG_BK; kk = e % SG_BK; }
+      else { ii = e % SG_BM; kk = e / SG_BM; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      float v = (gi < g.M && gk < kend) ? A[gi * g.a_rs + gk * g.a_cs] : 0.f;
+      As[kk][ii] = g.round_a ? bf16_round(v) : v;
+      int jj, kb;
+      if (b_jfast) { jj = e % SG_BN; kb = e / SG_BN; }
+      else { jj = e / SG_BK; kb = e % SG_BK; }
+      const int gj = j0 + jj, gkb = k0 + kb;
+      float w = (gj < g.N && gkb < kend) ? B[gkb * g.b_rs + gj * g.b_cs] : 0.f;
+      Bs[kb][jj] = g.round_b ? bf16_round(w) : w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) a[x] = As[kk][ty + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tx + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int i = i0 + ty + 16 * x;
+    if (i >= g.M) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int j = j0 + tx + 16 * y;
+      if (j >= g.N) continue;
+      const long long ci = bz * g.c_bs + i * g.c_rs + j * g.c_cs;
+      const long long co = ci + (ks > 1 ? sk * g.c_ss : 0);
+      float v = g.alpha * acc[x][y];
+      if (g.beta != 0.f) v += g.beta * g.C[co];
+      if (g.epi == SG_BIAS || g.epi == SG_BIAS_GELU) v += g.bias[i];
+      if (g.epi == SG_RESID) v += g.R[ci] + (g.bias ? g.bias[i] : 0.f);
+      if (g.round_c) v = bf16_round(v);
+      g.C[co] = v;
+      if (g.epi == SG_BIAS_GELU) g.C2[ci] = gelu(v);
+    }
+  }
+}
+
+// h0[b][c][i] = Wl[c][0] u[b][i] + Wl[c][1] a[b] + bl[c]
+__global__ void lift_kernel(const float* __restrict__ u, const float* __restrict__ a, const float* __restrict__ Wl,
+                            const float* __restrict__ bl, float* __restrict__ h, int B, int C, long long npix) {
+  const long long total = (long long)B * C * npix;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % npix;
+    const int c = (int)((e / npix) % C), b = (int)(e / (npix * C));
+    h[e] = Wl[2 * c] * u[(long long)b * npix + i] + Wl[2 * c + 1] * a[b] + bl[c];
+  }
+}
+
+// dz = dh * gelu'(z)
+__global__ void gelu_backward_kernel(const float* __restrict__ dh, const float* __restrict__ z, float* __restrict__ dz,
+                                     long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dz[e] = dh[e] * gelu_grad(z[e]);
+}
+
+// du = 2 (u_hat - target) / count; per-block partial sums of (u_hat - target)^2 in FP64
+__global__ void __launch_bounds__(256) mse_grad_kernel(const float* __restrict__ uh, const float* __restrict__ tg,
+                                                       float* __restrict__ du, long long n, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  const float scale = 2.f / (float)n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float d = uh[e] - tg[e];
+    du[e] = scale * d;
+    s += (double)d * d;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// part[(bc) * gridDim.x + blk] = partial sums over pixels of X[bc][i] * (y ? y[b][i] : 1), for
+// bc = b * C + c = blockIdx.y
+__global__ void __launch_bounds__(256) chan_dot_kernel(const float* __restrict__ X, const float* __restrict__ y,
+                                                       int C, long long npix, float* __restrict__ part) {
+  __shared__ float sh[256];
+  const int bc = blockIdx.y, b = bc / C;
+  const float* x = X + (long long)bc * npix;
+  const float* yy = y ? y + (long long)b * npix : nullptr;
+  float s = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x)
+    s += yy ? x[i] * yy[i] : x[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)bc * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// out[c * stride] (+)= sum_b w[b] sum_k part[(b * C + c) * nblk + k]   (w = NULL: weights 1)
+__global__ void chan_combine_kernel(const float* __restrict__ part, int nblk, const float* __restrict__ w, int B, int C,
+                                    float* __restrict__ out, int stride, int accumulate) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) {
+    float t = 0.f;
+    for (int k = 0; k < nblk; ++k) t += part[((long long)b * C + c) * nblk + k];
+    s += (w ? w[b] : 1.f) * t;
+  }
+  out[(long long)c * stride] = accumulate ? out[(long long)c * stride] + s : s;
+}
+
+// out[x] = sum_b in[b * X + x] (+ out[x] when accumulate)
+__global__ void reduce_batch_kernel(const float* __restrict__ in, float* __restrict__ out, int B, long long X,
+                                    int accumulate) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < X; x += (long long)gridDim.x * blockDim.x) {
+    float s = accumulate ? out[x] : 0.f;
+    for (int b = 0; b < B; ++b) s += in[(long long)b * X + x];
+    out[x] = s;
+  }
+}
+
+// Adam with bias correction (c1 = 1 - b1^t, c2 = 1 - b2^t)
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float gr = g[e];
+    const float mm = b1 * m[e] + (1.f - b1) * gr;
+    const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
+    m[e] = mm;
+    v[e] = vv;
+    w[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  }
+}
+
+// Parareal update V = Gn + F - Go, and per-problem squared norms of V and of V - U (FP64 partials,
+// one block row per problem: blockIdx.y = problem)
+__global__ void __launch_bounds__(256) parareal_update_kernel(const float* __restrict__ Gn, const float* __restrict__ F,
+                                                              const float* __restrict__ Go, const float* __restrict__ U,
+                                                              float* __restrict__ V, long long npix,
+                                                              double* __restrict__ part /* [B][gridDim.x][2] */) {
+  __shared__ double s0[256], s1[256];
+  const long long base = (long long)blockIdx.y * npix;
+  double a = 0.0, d = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+    const float v = Gn[base + i] + F[base + i] - Go[base + i];
+    V[base + i] = v;
+    const float e = v - U[base + i];
+    a += (double)v * v;
+    d += (double)e * e;
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = d;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) {
+      s0[threadIdx.x] += s0[threadIdx.x + k];
+      s1[threadIdx.x] += s1[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 2 + 0] = s0[0];
+    part[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 2 + 1] = s1[0];
+  }
+}
+
+}  // namespace sno
+}  // namespace etd

@@ -1,0 +1,146 @@
+"""Spectral neural operator and Parareal on the GPU against the CPU oracle (oracle/sno.py,
+oracle/etd.py), through the C ABI of include/etd_sno.h.
+
+Tolerances: the forward pass and the gradient are FP32 contractions over at most N^2 terms with
+the same bf16 rounding points as the oracle (which rounds the same float32 values); rel L2 2e-4
+for the operator's increment u_hat - u, 2e-3 per gradient array (sums over a batch of fields with
+cancellation). Parareal after as many iterations as windows reproduces the fine solver from the
+initial value exactly (up to rounding), so it is held to the FP32 long-horizon bound 3e-5 against
+the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import etd as oetd
+from oracle import sno as osno
+from paper_2209_11922_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = inputs.SnoWorkload("small", N=32, C=8, M=6, L=2, window=5, tau=1e-2)
+
+
+def _params(w):
+    P = w.init_weights()
+    P["bl"] = P["bl"] + 0.05
+    P["bp"] = P["bp"] - 0.02
+    P["bq"] = np.array(0.01)
+    P["Wq"] = P["Wq"] * 10
+    return P
+
+
+def _oparams(P):
+    return osno.Params(*[np.asarray(P[n], dtype=np.float32).astype(np.float64) for n in osno.Params.NAMES])
+
+
+def _fields(w, idx):
+    return np.stack([w.u0(i) for i in idx]).astype(np.float32)
+
+
+def _sno(w, B):
+    from paper_2209_11922_gb300.sno import Sno
+    return Sno(w.N, w.C, w.M, w.L, B)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_forward_matches_oracle():
+    w, B = SMALL, 3
+    P = _params(w)
+    u = _fields(w, range(B))
+    D = [w.D(i) for i in range(B)]
+    ref, _ = osno.forward(_oparams(P), u.astype(np.float64), D, w.N)
+    s = _sno(w, 4)
+    s.set_params(P)
+    got = s.forward(torch.from_numpy(u).cuda(), D).cpu().numpy()
+    assert _rel(got - u, ref - u) <= 2e-4
+
+
+def test_gradient_matches_oracle():
+    w, B = SMALL, 3
+    P = _params(w)
+    u = _fields(w, range(B))
+    tgt = (u + 0.1 * _fields(w, range(10, 10 + B))).astype(np.float32)
+    D = [w.D(i) for i in range(B)]
+    OP = _oparams(P)
+    uh, cache = osno.forward(OP, u.astype(np.float64), D, w.N)
+    g_ref = osno.backward(OP, cache, uh, tgt.astype(np.float64), w.N)
+    s = _sno(w, B)
+    s.set_params(P)
+    loss, g = s.gradient(torch.from_numpy(u).cuda(), D, torch.from_numpy(tgt).cuda())
+    assert abs(loss - osno.loss(uh, tgt)) <= 1e-4 * osno.loss(uh, tgt)
+    for n in osno.Params.NAMES:
+        assert _rel(g[n], getattr(g_ref, n)) <= 2e-3, n
+
+
+def test_adam_step_matches_oracle():
+    w, B = SMALL, 2
+    P = _params(w)
+    u = _fields(w, range(B))
+    tgt = (u + 0.1 * _fields(w, range(20, 20 + B))).astype(np.float32)
+    D = [w.D(i) for i in range(B)]
+    OP = _oparams(P)
+    uh, cache = osno.forward(OP, u.astype(np.float64), D, w.N)
+    opt = osno.Adam(lr=1e-3)
+    opt.step(OP, osno.backward(OP, cache, uh, tgt.astype(np.float64), w.N))
+    s = _sno(w, B)
+    s.set_params(P)
+    s.train_step(torch.from_numpy(u).cuda(), D, torch.from_numpy(tgt).cuda(), 1e-3)
+    got = s.get_params()
+    for n in osno.Params.NAMES:
+        # each weight moves by about lr; a gradient entry near zero may round to the other sign
+        moved = np.abs(np.asarray(got[n]) - getattr(OP, n))
+        assert np.mean(moved <= 2e-5 + 1e-6 * np.abs(getattr(OP, n))) >= 0.99, n
+
+
+def test_training_lowers_the_loss():
+    w, B = SMALL, 4
+    s = _sno(w, B)
+    s.set_params(_params(w))
+    u = torch.from_numpy(_fields(w, range(B))).cuda()
+    tgt = torch.from_numpy(0.5 * _fields(w, range(B))).cuda()
+    D = [w.D(i) for i in range(B)]
+    first = s.train_step(u, D, tgt, 3e-3)
+    for _ in range(30):
+        last = s.train_step(u, D, tgt, 3e-3)
+    assert last < 0.5 * first
+
+
+@pytest.mark.parametrize("coarse", ["sno", "etdrk2"])
+def test_parareal_with_all_iterations_is_the_fine_solution(coarse):
+    """After as many iterations as windows Parareal reproduces the sequential fine solve."""
+    from paper_2209_11922_gb300.sno import Parareal
+    w, B, W = SMALL, 2, 3
+    u0 = _fields(w, range(B))
+    D = [w.D(i) for i in range(B)]
+    s = None
+    if coarse == "sno":
+        s = _sno(w, B)
+        s.set_params(_params(w))
+    pr = Parareal(s, w.N, D, w.tau, w.window, W)
+    out, st = pr.run(torch.from_numpy(u0).cuda(), max_iter=W, tol=0.0, fallback_tol=1e9)
+    assert st["iterations"] == W and st["fallbacks"] == 0
+    got = out.cpu().numpy()
+    for b in range(B):
+        ref = oetd.run(u0[b].astype(np.float64), (w.N, w.N), (1 / w.N, 1 / w.N), D[b], w.tau, W * w.window, 2)
+        assert _rel(got[b], ref) <= 3e-5
+
+
+def test_parareal_fallback_advances_rejected_windows_with_the_fine_solver():
+    """With a zero fallback threshold every window with a nonzero correction in the second iteration
+    is recomputed by the fine solver (all but the first, which the first iteration already made
+    exact), so two iterations give the fine solution."""
+    from paper_2209_11922_gb300.sno import Parareal
+    w, B, W = SMALL, 2, 4
+    u0 = _fields(w, range(30, 30 + B))
+    D = [w.D(i) for i in range(B)]
+    pr = Parareal(None, w.N, D, w.tau, w.window, W)
+    out, st = pr.run(torch.from_numpy(u0).cuda(), max_iter=2, tol=0.0, fallback_tol=0.0)
+    assert st["iterations"] == 2 and st["fallbacks"] == W - 1
+    got = out.cpu().numpy()
+    for b in range(B):
+        ref = oetd.run(u0[b].astype(np.float64), (w.N, w.N), (1 / w.N, 1 / w.N), D[b], w.tau, W * w.window, 2)
+        assert _rel(got[b], ref) <= 3e-5
