@@ -375,6 +375,110 @@ def run_batched(args, bw):
     return 0
 
 
+def run_sno_parareal(args, sw):
+    """Parareal with the trained SNO as coarse propagator against the plain batched ETDRK2 solver on
+    B problems at N x N (windows x window steps). Training (data from the plain solver, Adam) runs
+    before the timed region. Also times Parareal with a non-learned coarse propagator (one ETDRK2
+    step of window * tau) to show what the learning gains."""
+    import torch
+
+    from paper_2209_11922_gb300.etd import Batch
+    from paper_2209_11922_gb300.sno import Parareal, Sno
+    from paper_2209_11922_gb300.sno_train import make_pairs, rel_error, train
+
+    world, rank, local = _dist_setup(args)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    B, W, n = sw.batch, sw.windows, sw.N - 1
+    ntraj = args.sno_trajectories or sw.trajectories
+    t0 = time.perf_counter()
+    u_in, u_out, Dtr = make_pairs(sw, range(ntraj))
+    t_data = time.perf_counter() - t0
+    nval = max(B, u_in.shape[0] // 20)
+    sno = Sno(sw.N, sw.C, sw.M, sw.L, B)
+    sno.set_params(sw.init_weights())
+    t0 = time.perf_counter()
+    hist = train(sno, u_in[nval:], u_out[nval:], Dtr[nval:], args.sno_epochs, B, lr=args.sno_lr, seed=sw.seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val = rel_error(sno, u_in[:nval], u_out[:nval], Dtr[:nval], B)
+    del u_in, u_out
+    torch.cuda.empty_cache()
+    # test problems: seeds beyond the training trajectories
+    tid = [10 ** 6 + b for b in range(B)]
+    D = [sw.D(i) for i in tid]
+    u0 = torch.from_numpy(np.stack([sw.u0(i) for i in tid]).astype(np.float32)).cuda()
+    plain = Batch([(sw.N, sw.N)] * B, D, sw.tau, 2, "f32")
+    work = torch.empty_like(u0)
+    steps = W * sw.window
+
+    def run_plain():
+        work.copy_(u0)
+        plain.run([work[b] for b in range(B)], steps, stream)
+
+    pr_sno = Parareal(sno, sw.N, D, sw.tau, sw.window, W)
+    pr_big = Parareal(None, sw.N, D, sw.tau, sw.window, W)
+    out = torch.empty_like(u0)
+    stats = {}
+
+    def run_pr(pr, key):
+        _, st = pr.run(u0, W, args.sno_tol, 1e-2, out=out, stream=stream)
+        stats[key] = st
+
+    def timed(fn, k):
+        tot = 0.0
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / k
+
+    timed(run_plain, args.warmup)
+    ref = work.clone()
+    with ClockSampler(local) as clk:
+        ms_plain = timed(run_plain, args.steps)
+        timed(lambda: run_pr(pr_sno, "sno"), args.warmup)
+        ms_sno = timed(lambda: run_pr(pr_sno, "sno"), args.steps)
+    err = lambda a: float(max((torch.linalg.vector_norm(a[b] - ref[b]) / torch.linalg.vector_norm(ref[b])).item()
+                              for b in range(B)))
+    err_sno = err(out)
+    timed(lambda: run_pr(pr_big, "big"), 1)
+    ms_big = timed(lambda: run_pr(pr_big, "big"), max(1, args.steps // 2))
+    err_big = err(out)
+    # the coarse propagator alone (one SNO application to B fields)
+    g = torch.empty_like(u0)
+    ms_coarse = timed(lambda: sno.forward(u0, D, out=g, stream=stream), args.steps)
+    fl = 2.0 * B * sw.C * sw.L * (2 * (n * n * sw.M + n * sw.M * sw.M) + sw.C * n * n)   # GEMM flops
+    achieved = fl / (ms_coarse * 1e-3) / 1e12
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock (TFLOP/s)
+    line = {
+        "metric": "surrogate vs plain speedup at L2 err", "value": ms_plain / ms_sno, "unit": "x", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_sno, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 mode mix)", "data": "synthetic",
+        "config": {"workload": sw.name, "problems": B, "mesh": [sw.N, sw.N], "windows": W,
+                   "window_steps": sw.window, "tau": sw.tau, "channels": sw.C, "modes": sw.M, "layers": sw.L,
+                   "train_trajectories": ntraj, "train_pairs": int(ntraj * W), "epochs": args.sno_epochs,
+                   "train_s": round(t_train, 1), "data_s": round(t_data, 1),
+                   "train_loss": [float("%.4g" % v) for v in hist], "val_rel_l2_one_window": val,
+                   "tol": args.sno_tol, "fallback_tol": 1e-2},
+        "plain_ms": ms_plain, "parareal_sno_ms": ms_sno, "parareal_sno": stats["sno"], "final_rel_l2_sno": err_sno,
+        "parareal_etdrk2_coarse_ms": ms_big, "parareal_etdrk2_coarse": stats["big"], "final_rel_l2_etdrk2": err_big,
+        "gain_vs_nonlearned_coarse": ms_big / ms_sno, "coarse_sno_ms": ms_coarse,
+        "gpu_launches": None,
+        "roofline": {"bound": "alu", "kernel": "SNO forward (strided batched FP32 GEMMs)", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "traffic": None},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    for o in (pr_sno, pr_big, sno, plain):
+        o.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,17 +486,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=inputs.AC2D_1024.name,
-                    choices=sorted(inputs.WORKLOADS) + sorted(inputs.BATCH_WORKLOADS))
+                    choices=sorted(inputs.WORKLOADS) + sorted(inputs.BATCH_WORKLOADS) + sorted(inputs.SNO_WORKLOADS))
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--route", default="auto", choices=["auto", "fft", "fft_half", "gemm_tf32", "gemm_bf16x3"])
     ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time-step count")
     ap.add_argument("--ref-sample-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sno-trajectories", type=int, default=0, help="training trajectories (default: the workload's)")
+    ap.add_argument("--sno-epochs", type=int, default=6)
+    ap.add_argument("--sno-lr", type=float, default=1e-3)
+    ap.add_argument("--sno-tol", type=float, default=1e-4, help="Parareal stopping correction")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.workload in inputs.BATCH_WORKLOADS:
         return run_batched(args, inputs.BATCH_WORKLOADS[args.workload])
+    if args.workload in inputs.SNO_WORKLOADS:
+        return run_sno_parareal(args, inputs.SNO_WORKLOADS[args.workload])
     w = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
