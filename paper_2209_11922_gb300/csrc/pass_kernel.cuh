@@ -309,21 +309,30 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   C* const b0p = b0 + p * LP;
   C* const b1p = b1 + p * LP;
   C* const scrp = scr + p * (TPP > 32 ? TPP / 32 : 1);
-  const T tau = A.tau, c2 = A.c2, flin = A.flin, fcub = A.fcub;
+  const T tau = A.tau, c2 = A.c2, flin = A.flin, fcub = A.fcub, inv_c2 = T(1) / A.c2;
 
   auto epilogue = [&](int kind, int j, C w) -> C {
     if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
     const T zjj = zj[j], ejj = ej[j];
     T out[2];
     const T wv[2] = {w.x, w.y};
+    // phi_k(-zeta) in closed form for zeta >= 1 from one reciprocal per mode; the series runs only
+    // in warps holding a mode below zeta = 1 (or c2 zeta = 1), the low-mode corner of the spectrum
+    // (every lane of the warp votes with its own predicate, so a lane that needs it gets it).
+    const unsigned act = __activemask();
     if (kind == EPI_RK1) {
       const C u = b0p[L::at(j)];
       const T uv[2] = {u.x, u.y};
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const T zeta = pz[t] + zjj, E = pe[t] * ejj;
-        const T rz = zeta < T(1) ? T(0) : recip(zeta);
-        out[t] = E * uv[t] + tau * phi1_only(zeta, E, rz) * wv[t];
+        const bool small = zeta < T(1);
+        T p1 = (T(1) - E) * rcp_rn(small ? T(1) : zeta);
+        if (__any_sync(act, small)) {
+          const T s2 = phi2_series<T>(small ? -zeta : T(0));
+          p1 = small ? T(1) - zeta * s2 : p1;
+        }
+        out[t] = E * uv[t] + tau * p1 * wv[t];
       }
       b0p[L::at(j)] = C{out[0], out[1]};
       return w;
@@ -335,14 +344,25 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       T u2[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj;
-        const T zc = c2 * zeta;
-        const T rz = zc < T(1) ? (zeta < T(1) ? T(0) : recip(zeta)) : recip(zeta);
-        T p1, p2;
-        phi12(zeta, E, rz, p1, p2);
-        const T p1c = phi1_only(zc, Ec, rz / c2);
-        u2[t] = Ec * uv[t] + c2 * tau * p1c * wv[t];
-        out[t] = E * uv[t] + tau * (p1 - p2 / c2) * wv[t];
+        const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj, zc = c2 * zeta;
+        const bool small = zeta < T(1);
+        const T rz = rcp_rn(small ? T(1) : zeta);
+        T p1 = (T(1) - E) * rz;
+        T p2 = (T(1) - p1) * rz;
+        if (__any_sync(act, small)) {
+          const T s2 = phi2_series<T>(small ? -zeta : T(0));
+          p2 = small ? s2 : p2;
+          p1 = small ? T(1) - zeta * s2 : p1;
+        }
+        // c2 tau phi1(-c2 zeta) = tau (1 - Ec) / zeta for c2 zeta >= 1
+        T t1 = tau * (T(1) - Ec) * rz;
+        const bool smc = zc < T(1);
+        if (__any_sync(act, smc)) {
+          const T s2c = phi2_series<T>(smc ? -zc : T(0));
+          t1 = smc ? c2 * tau * (T(1) - zc * s2c) : t1;
+        }
+        u2[t] = Ec * uv[t] + t1 * wv[t];
+        out[t] = E * uv[t] + tau * (p1 - p2 * inv_c2) * wv[t];
       }
       b0p[L::at(j)] = C{u2[0], u2[1]};
       return C{out[0], out[1]};
@@ -353,10 +373,14 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const T zeta = pz[t] + zjj, E = pe[t] * ejj;
-      const T rz = zeta < T(1) ? T(0) : recip(zeta);
-      T p1, p2;
-      phi12(zeta, E, rz, p1, p2);
-      out[t] = pv[t] + (tau / c2) * p2 * wv[t];
+      const bool small = zeta < T(1);
+      const T rz = rcp_rn(small ? T(1) : zeta);
+      T p2 = (T(1) - (T(1) - E) * rz) * rz;
+      if (__any_sync(act, small)) {
+        const T s2 = phi2_series<T>(small ? -zeta : T(0));
+        p2 = small ? s2 : p2;
+      }
+      out[t] = pv[t] + (tau * inv_c2) * p2 * wv[t];
     }
     return C{out[0], out[1]};
   };
