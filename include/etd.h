@@ -78,7 +78,13 @@ typedef struct {
   double c2;         /* EIFE2 stage node c_2 in (0, 1]; default 0.5 (Section 5) */
   double flin;       /* f(u) = flin*u + fcub*u^3; defaults 1 and -1 (Allen-Cahn) */
   double fcub;
+  int debug;         /* default 0. ETD_DEBUG_STALL_FIRST_GEMM_PASS (GEMM routes): the first tensor-core
+                        pass of every etd_run withholds its accumulator-ready signal, so that pass's
+                        epilogue warps wait out their 2 s limit, abort and set the plan's error word;
+                        the next synchronising call returns ETD_ERR_TIMEOUT and that run's field is
+                        invalid. Tests the failure path; any other value is ignored. */
 } etd_options;
+#define ETD_DEBUG_STALL_FIRST_GEMM_PASS 0x5A11
 
 /* Fill *opt with the defaults above. Returns ETD_ERR_INVALID_ARG if opt is NULL. */
 etd_status etd_options_default(etd_options* opt);

@@ -451,7 +451,7 @@ etd_status upload_gemm_tables(etd_plan_s* pl) {
 // One tensor-core pass contracting paper axis a of field `in` (pitched, axis a contiguous):
 // out0[k * R + r] = epi((in S_a)[r][k]).
 etd_status make_gemm_launch(etd_plan_s* pl, int a, const void* in, const void* in1, void* out0, void* out1, int op,
-                            int kind, double fields_rw, Launch& L) {
+                            int kind, double fields_rw, Launch& L, bool stall = false) {
   const int K = (int)pl->N[a];
   const int R = (int)(pl->nfield / (size_t)K);
   const int route = pl->gemm - 1;
@@ -506,6 +506,7 @@ etd_status make_gemm_launch(etd_plan_s* pl, int a, const void* in, const void* i
   g.flin = (float)pl->opt.flin;
   g.fcub = (float)pl->opt.fcub;
   g.err = pl->dev_err;
+  g.stall = stall ? 1 : 0;
   L.fn = k->fn;
   L.grid = dim3((unsigned)(mt * nt));
   L.block = dim3((unsigned)k->threads);
@@ -566,7 +567,9 @@ etd_status entry_exit_gemm(etd_plan_s* pl, bool entry, void* u, std::vector<Laun
   int cur = V;
   for (int p = 0; p < d; ++p) {
     const int dst = (entry && p == d - 1) ? V : (p % 2 == 0 ? T1 : T2);
-    if ((st = make_gemm_launch(pl, p, F[cur], nullptr, F[dst], nullptr, GE_PLAIN, PK_ENTRY_EXIT, 2.0, L)) != ETD_OK)
+    const bool stall = entry && p == 0 && pl->opt.debug == ETD_DEBUG_STALL_FIRST_GEMM_PASS;
+    if ((st = make_gemm_launch(pl, p, F[cur], nullptr, F[dst], nullptr, GE_PLAIN, PK_ENTRY_EXIT, 2.0, L, stall)) !=
+        ETD_OK)
       return st;
     out.push_back(L);
     cur = dst;
@@ -1056,6 +1059,7 @@ etd_status etd_options_default(etd_options* opt) {
   opt->c2 = 0.5;
   opt->flin = 1.0;
   opt->fcub = -1.0;
+  opt->debug = 0;
   return ETD_OK;
 }
 

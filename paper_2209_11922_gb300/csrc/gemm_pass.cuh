@@ -48,6 +48,7 @@ struct GemmArgs {
   const float* zk; const float* ek; const float* ck;
   float tau, c2, flin, fcub;
   int* err;          // set to 1 by a CTA whose wait ran out
+  int stall;         // test of the failure path: the accumulator-ready signal is withheld
 };
 
 struct GemmParams {
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_pass_kernel(const __grid
         }
         umma::mma_commit(&empty[s]);
       }
-      umma::mma_commit(accf);
+      if (!g.stall) umma::mma_commit(accf);
       if (*abort_flag) umma::mbar_drain(accf, 0);   // MMAs in flight finish before TMEM is freed
     }
   } else {

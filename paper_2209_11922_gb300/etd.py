@@ -38,7 +38,7 @@ class Plan:
 
     def __init__(self, N: Sequence[int], D: float, tau: float, scheme: int = 2, dtype: str = "f64",
                  h: Optional[Sequence[float]] = None, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0,
-                 route: str = "auto"):
+                 route: str = "auto", debug: int = 0):
         L = nat.lib()
         self.N = tuple(int(n) for n in N)
         self.ndim = len(self.N)
@@ -51,6 +51,7 @@ class Plan:
         opt.dtype = _DT[dtype]
         opt.route = _ROUTE[route]
         opt.c2, opt.flin, opt.fcub = float(c2), float(flin), float(fcub)
+        opt.debug = int(debug)
         Na = (ctypes.c_int64 * 3)(*(list(self.N) + [1] * (3 - self.ndim)))
         ha = (ctypes.c_double * 3)(*(list(self.h) + [1.0] * (3 - self.ndim)))
         handle = ctypes.c_void_p()

@@ -117,3 +117,20 @@ def test_gemm_route_full_size_2d_1024_first_steps(route):
         d = torch.from_numpy(U0.astype(np.float32)).cuda()
         pl.run(d, 3)
         _check(d.cpu().numpy(), ref, route, w.name)
+
+
+def test_gemm_pass_wait_limit_reports_timeout_and_leaves_the_context_usable():
+    """Failure path of the tensor-core pass: with the debug option the first pass of a run never
+    receives its accumulator-ready signal; its epilogue warps give up after their 2 s limit, the
+    CTA frees its tensor memory and exits, and the next synchronising call reports
+    ETD_ERR_TIMEOUT. Another plan then runs correctly on the same context."""
+    from paper_2209_11922_gb300 import _native as nat
+    N, D, tau = (64, 64), 1e-2, 1e-2
+    U0 = _u0(N, 33).astype(np.float32)
+    with _plan(N, D, tau, 2, "gemm_tf32", debug=nat.ETD_DEBUG_STALL_FIRST_GEMM_PASS) as pl:
+        with pytest.raises(nat.EtdError) as ei:
+            pl.run_host(U0.copy(), 1)
+        assert ei.value.status == nat.ETD_ERR_TIMEOUT
+    ref = oetd.run(U0.astype(np.float64), N, [1.0 / n for n in N], D, tau, 2, 2)
+    with _plan(N, D, tau, 2, "gemm_tf32") as pl:
+        _check(pl.run_host(U0.copy(), 2), ref, "gemm_tf32", "after a timed-out run")
