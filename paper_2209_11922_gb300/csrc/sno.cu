@@ -102,13 +102,21 @@ struct GemmOp {
     g.C = p; g.c_rs = rs; g.c_cs = cs; g.c_bs = bs;
     return *this;
   }
-  etd_status run(cudaStream_t s) const {
+  template <int BM, int BN>
+  etd_status launch(cudaStream_t s) const {
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
-    dim3 grid((g.N + SG_BN - 1) / SG_BN, (g.M + SG_BM - 1) / SG_BM, g.batch * ks);
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * ks);
     if (grid.z > 65535u) return sfail(ETD_ERR_UNSUPPORTED, "GEMM batch %u too large", grid.z);
-    sgemm_kernel<<<grid, 256, 0, s>>>(g);
+    sgemm_kernel<BM, BN><<<grid, 256, 0, s>>>(g);
     SNO_CUDA(cudaGetLastError());
     return ETD_OK;
+  }
+  // tile shape by output shape: skinny outputs get skinny tiles, large ones 128 x 128
+  etd_status run(cudaStream_t s) const {
+    if (g.M <= 32) return launch<32, 128>(s);
+    if (g.N <= 32) return launch<128, 32>(s);
+    if (g.M >= 128 && g.N >= 128) return launch<128, 128>(s);
+    return launch<64, 64>(s);
   }
 };
 
@@ -180,7 +188,8 @@ etd_status sno_alloc(float** p, long long count) {
 etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStream_t s) {
   const int C = m->C, M = m->M, L = m->L;
   const long long np = m->npix, img = (long long)C * np, M2 = (long long)M * M;
-  lift_kernel<<<grid_for((long long)B * img), 256, 0, s>>>(u, m->a, m->W + m->oWl, m->W + m->obl, m->h[0], B, C, np);
+  lift_kernel<<<dim3(grid_for(np) < 64 ? grid_for(np) : 64, B * C), 256, 0, s>>>(u, m->a, m->W + m->oWl,
+                                                                               m->W + m->obl, m->h[0], B, C, np);
   SNO_CUDA(cudaGetLastError());
   for (int l = 0; l < L; ++l) {
     SNO_TRY(modes_of(m, m->h[l], B * C, m->hh[l], true, s));

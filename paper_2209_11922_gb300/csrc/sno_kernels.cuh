@@ -49,67 +49,82 @@ struct SGemm {
   long long c_ss;
 };
 
-constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
+constexpr int SG_BK = 16;
 
-// 256 threads, 4 x 4 outputs each; tiles staged in shared memory. A operand loads walk the
-// contiguous index of A (K when a_cs == 1, rows otherwise), same for B.
+// Tile BM x BN per CTA of 256 threads (16 x 16); thread (tx, ty) owns rows 2 ty + 32 a + {0, 1} and
+// columns 2 tx + 32 b + {0, 1} (pairs read as float2 from shared memory, and a warp's stores of one
+// row cover 128 contiguous bytes); K in steps of 16 through shared memory. Operand loads walk the
+// contiguous index of each operand. Shapes: 64 x 64 in general, 128 x 128 for large square
+// outputs, 32 x 128 / 128 x 32 for the skinny ones (C = 32 channels, M = 24 modes).
+template <int BM, int BN>
 __global__ void __launch_bounds__(256) sgemm_kernel(const SGemm g) {
-  __shared__ float As[SG_BK][SG_BM + 4];
-  __shared__ float Bs[SG_BK][SG_BN + 4];
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ __align__(16) float As[SG_BK][BM + 4];
+  __shared__ __align__(16) float Bs[SG_BK][BN + 4];
   const int ks = g.ksplit > 1 ? g.ksplit : 1;
   const int bz = blockIdx.z / ks, sk = blockIdx.z % ks;
   const int kc = ((g.K + ks - 1) / ks + SG_BK - 1) / SG_BK * SG_BK;   // K range of this split
   const int kbeg = sk * kc, kend = min(g.K, kbeg + kc);
-  const int i0 = blockIdx.y * SG_BM, j0 = blockIdx.x * SG_BN;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
   const float* A = g.A + bz * g.a_bs;
   const float* B = g.B + bz * g.b_bs;
-  float acc[4][4];
+  float acc[TM][TN];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < TN; ++b) acc[a][b] = 0.f;
   const bool a_kfast = g.a_cs == 1 || g.a_rs != 1;
   const bool b_jfast = g.b_cs == 1 || g.b_rs != 1;
   for (int k0 = kbeg; k0 < kend; k0 += SG_BK) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = t + 256 * r;   // 0..1023 over the 64 x 16 tile
+    for (int e = t; e < BM * SG_BK; e += 256) {
       int ii, kk;
       if (a_kfast) { ii = e / SG_BK; kk = e % SG_BK; }
-      else { ii = e % SG_BM; kk = e / SG_BM; }
+      else { ii = e % BM; kk = e / BM; }
       const int gi = i0 + ii, gk = k0 + kk;
-      float v = (gi < g.M && gk < kend) ? A[gi * g.a_rs + gk * g.a_cs] : 0.f;
+      const float v = (gi < g.M && gk < kend) ? A[gi * g.a_rs + gk * g.a_cs] : 0.f;
       As[kk][ii] = g.round_a ? bf16_round(v) : v;
+    }
+#pragma unroll
+    for (int e = t; e < BN * SG_BK; e += 256) {
       int jj, kb;
-      if (b_jfast) { jj = e % SG_BN; kb = e / SG_BN; }
+      if (b_jfast) { jj = e % BN; kb = e / BN; }
       else { jj = e / SG_BK; kb = e % SG_BK; }
       const int gj = j0 + jj, gkb = k0 + kb;
-      float w = (gj < g.N && gkb < kend) ? B[gkb * g.b_rs + gj * g.b_cs] : 0.f;
+      const float w = (gj < g.N && gkb < kend) ? B[gkb * g.b_rs + gj * g.b_cs] : 0.f;
       Bs[kb][jj] = g.round_b ? bf16_round(w) : w;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < SG_BK; ++kk) {
-      float a[4], b[4];
+      float a[TM], b[TN];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) a[x] = As[kk][ty + 16 * x];
+      for (int x = 0; x < TM; x += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(&As[kk][2 * ty + 16 * x]);
+        a[x] = v.x;
+        a[x + 1] = v.y;
+      }
 #pragma unroll
-      for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tx + 16 * y];
+      for (int y = 0; y < TN; y += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(&Bs[kk][2 * tx + 16 * y]);
+        b[y] = v.x;
+        b[y + 1] = v.y;
+      }
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < TM; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        for (int y = 0; y < TN; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int i = i0 + ty + 16 * x;
+  for (int x = 0; x < TM; ++x) {
+    const int i = i0 + 2 * ty + 16 * (x & ~1) + (x & 1);
     if (i >= g.M) continue;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int j = j0 + tx + 16 * y;
+    for (int y = 0; y < TN; ++y) {
+      const int j = j0 + 2 * tx + 16 * (y & ~1) + (y & 1);
       if (j >= g.N) continue;
       const long long ci = bz * g.c_bs + i * g.c_rs + j * g.c_cs;
       const long long co = ci + (ks > 1 ? sk * g.c_ss : 0);
@@ -124,15 +139,15 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const SGemm g) {
   }
 }
 
-// h0[b][c][i] = Wl[c][0] u[b][i] + Wl[c][1] a[b] + bl[c]
+// h0[b][c][i] = Wl[c][0] u[b][i] + Wl[c][1] a[b] + bl[c]; blockIdx.y = b * C + c
 __global__ void lift_kernel(const float* __restrict__ u, const float* __restrict__ a, const float* __restrict__ Wl,
                             const float* __restrict__ bl, float* __restrict__ h, int B, int C, long long npix) {
-  const long long total = (long long)B * C * npix;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e % npix;
-    const int c = (int)((e / npix) % C), b = (int)(e / (npix * C));
-    h[e] = Wl[2 * c] * u[(long long)b * npix + i] + Wl[2 * c + 1] * a[b] + bl[c];
-  }
+  const int bc = blockIdx.y, b = bc / C, c = bc - b * C;
+  const float w0 = Wl[2 * c], off = Wl[2 * c + 1] * a[b] + bl[c];
+  const float* ub = u + (long long)b * npix;
+  float* hb = h + (long long)bc * npix;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x)
+    hb[i] = w0 * ub[i] + off;
 }
 
 // dz = dh * gelu'(z)
