@@ -120,6 +120,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _job_throughput(ms_local: float, updates_per_rank: float, world: int, device: str = "cuda"):
+    """Whole-job throughput of `world` replicas: the slowest rank's time (max over ranks, one
+    all-reduce; the caller brackets the timed region with barriers) and the updates of all ranks
+    divided by it. Returns (ms_max, updates_per_s)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, updates_per_rank * world / (ms_max * 1e-3)
+
+
+def _job_e2e(per_rank_value: float, world: int, device: str = "cuda") -> float:
+    """End-to-end whole-job throughput: the slowest rank's rate times the number of ranks."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(per_rank_value)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return float(t.item()) * world
+
+
 def _dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -220,12 +245,7 @@ def run_gb300(args, w):
         dist.barrier()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    updates = float(w.unknowns) * nsteps * args.steps * world
-    value = updates / (ms_max * 1e-3)
+    ms_max, value = _job_throughput(ms, float(w.unknowns) * nsteps * args.steps, world)
     nonfinite = plan.monitor(u)["nonfinite"]
 
     # kernel-level timing of the same workload (separate run, events around every launch)
@@ -240,7 +260,7 @@ def run_gb300(args, w):
     alg_bytes = rw * w.unknowns * esz
     achieved = alg_bytes / (dom_ms * 1e-3 / dom_n) / 1e9
     peak, peak_src = _peaks()
-    traffic = _traffic(f"{w.name}:{dtype}:{dom}")
+    traffic = _traffic(f"{w.name}:{dtype}:{args.route}:{dom}")
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hbuf = torch.empty(u0.shape, dtype=tdt, pin_memory=True).numpy()
@@ -254,11 +274,7 @@ def run_gb300(args, w):
         t0 = time.perf_counter()
         plan.run_host(hbuf, nsteps)
         e2e_t += time.perf_counter() - t0
-    e2e_val = float(w.unknowns) * nsteps * args.steps / e2e_t
-    if world > 1:
-        t = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MIN)
-        e2e_val = float(t.item()) * world
+    e2e_val = _job_e2e(float(w.unknowns) * nsteps * args.steps / e2e_t, world)
 
     if rank == 0:
         clocks = clk.summary()
