@@ -41,6 +41,14 @@ template <class T> __device__ __forceinline__ T phi1_only(T zeta, T E, T rz) {
 // 1/zeta (zeta > 0 where it is used): one division per mode serves every phi of the mode.
 template <class T> __device__ __forceinline__ T recip(T z) { return T(1) / z; }
 
+// Hardware reciprocal approximation (one MUFU instruction, within 1 ulp; flushes denormals), for
+// the tensor-core routes whose operand rounding is far coarser.
+__device__ __forceinline__ float rcp_approx(float z) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(z));
+  return r;
+}
+
 // Correctly rounded reciprocal (the same value as 1/z).
 __device__ __forceinline__ float rcp_rn(float z) { return __frcp_rn(z); }
 __device__ __forceinline__ double rcp_rn(double z) { return __drcp_rn(z); }

@@ -114,14 +114,14 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
     }
   }
   const float tau = g.tau, c2 = g.c2, flin = g.flin, fcub = g.fcub, inv_c2 = 1.f / g.c2;
-  const size_t R = (size_t)g.R;
+  const int R = g.R;   // fields hold < 2^31 values: per-column offsets j * R in 32 bits
   for (int c0 = cb; c0 < ce; c0 += 16) {
     float v[16];
     umma::tmem_ld16(trow + (uint32_t)c0, v);   // warp-collective: every lane takes part
     if (!row_ok) continue;
     const int kb = n0 + c0;
     const int nv = g.K - kb < 16 ? g.K - kb : 16;   // valid columns of this chunk
-    float* o0 = g.out0 + (size_t)kb * R + r;
+    float* o0 = g.out0 + (size_t)kb * (size_t)R + r;
     if (op == GE_PLAIN) {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
@@ -135,14 +135,14 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
       continue;
     }
     // spectral combination: all loads of the chunk are issued before any arithmetic
-    const float* i1 = g.in1 + (size_t)kb * R + r;
+    const float* i1 = g.in1 + (size_t)kb * (size_t)R + r;
     float w[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) w[j] = j < nv ? i1[j * R] : 0.f;
     const float* tz = tabs + c0;
     const float* te = tabs + BN + c0;
     const float* tc = tabs + 2 * BN + c0;
-    float* o1 = op == GE_S1 ? g.out1 + (size_t)kb * R + r : nullptr;
+    float* o1 = op == GE_S1 ? g.out1 + (size_t)kb * (size_t)R + r : nullptr;
     // phi_k(-zeta) in closed form for zeta >= 1 (one reciprocal per mode serves phi_1, phi_2 and
     // the c2 stage); the series is evaluated only by warps holding a mode that needs it
     // (zeta < 1, or c2 zeta < 1 in the first stage) - the low-mode corner of the spectrum. Rows
@@ -151,7 +151,7 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const float zeta = zr + tz[j], E = er * te[j];
-      const float rz = rcp_rn(fmaxf(zeta, 1.f));
+      const float rz = rcp_approx(fmaxf(zeta, 1.f));   // 1 ulp: far below the route's TF32 / bf16 error
       float p1 = (1.f - E) * rz, p2 = (1.f - p1) * rz;
       const bool small = zeta < 1.f;
       if (__any_sync(act, small)) {
