@@ -115,6 +115,17 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
   }
   const float tau = g.tau, c2 = g.c2, flin = g.flin, fcub = g.fcub, inv_c2 = 1.f / g.c2;
   const int R = g.R;   // fields hold < 2^31 values: per-column offsets j * R in 32 bits
+  // second input of the spectral passes, one chunk ahead: the loads of chunk c + 16 are in flight
+  // while chunk c is computed
+  float wn[16];
+  auto load_w = [&](int c) {
+    const int kb = n0 + c;
+    const int nv = g.K - kb < 16 ? g.K - kb : 16;
+    const float* i1 = g.in1 + (size_t)kb * (size_t)R + r;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) wn[j] = j < nv ? i1[j * R] : 0.f;
+  };
+  if (spectral && row_ok && cb < ce) load_w(cb);
   for (int c0 = cb; c0 < ce; c0 += 16) {
     float v[16];
     umma::tmem_ld16(trow + (uint32_t)c0, v);   // warp-collective: every lane takes part
@@ -134,11 +145,11 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
         if (j < nv) o0[j * R] = v[j] * (flin + fcub * v[j] * v[j]);
       continue;
     }
-    // spectral combination: all loads of the chunk are issued before any arithmetic
-    const float* i1 = g.in1 + (size_t)kb * (size_t)R + r;
+    // spectral combination
     float w[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) w[j] = j < nv ? i1[j * R] : 0.f;
+    for (int j = 0; j < 16; ++j) w[j] = wn[j];
+    if (c0 + 16 < ce) load_w(c0 + 16);
     const float* tz = tabs + c0;
     const float* te = tabs + BN + c0;
     const float* tc = tabs + 2 * BN + c0;

@@ -57,7 +57,7 @@ constexpr int SG_BK = 16;
 // contiguous index of each operand. Shapes: 64 x 64 in general, 128 x 128 for large square
 // outputs, 32 x 128 / 128 x 32 for the skinny ones (C = 32 channels, M = 24 modes).
 template <int BM, int BN>
-__global__ void __launch_bounds__(256) sgemm_kernel(const SGemm g) {
+__global__ void __launch_bounds__(256, 2) sgemm_kernel(const SGemm g) {
   constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ __align__(16) float As[SG_BK][BM + 4];
   __shared__ __align__(16) float Bs[SG_BK][BN + 4];
