@@ -154,15 +154,42 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
     const float* te = tabs + BN + c0;
     const float* tc = tabs + 2 * BN + c0;
     float* o1 = op == GE_S1 ? g.out1 + (size_t)kb * (size_t)R + r : nullptr;
-    // phi_k(-zeta) in closed form for zeta >= 1 (one reciprocal per mode serves phi_1, phi_2 and
-    // the c2 stage); the series is evaluated only by warps holding a mode that needs it
-    // (zeta < 1, or c2 zeta < 1 in the first stage) - the low-mode corner of the spectrum. Rows
-    // come in whole warps (R is a multiple of 32), so every lane of a warp reaches the votes.
+    // phi_k(-zeta) in closed form for zeta >= 1: one reciprocal per mode serves phi_1, phi_2 and
+    // the c2 stage. The modes grow along the column axis, so the smallest zeta of this chunk is at
+    // its first column: a warp none of whose rows needs the series there (zeta < 1, or
+    // c2 zeta < 1 in the first stage) takes the closed-form-only loop for all 16 columns; warps
+    // in the low-mode corner of the spectrum take the general loop. Rows come in whole warps (R is
+    // a multiple of 32), so every lane of a warp reaches the vote.
     const unsigned act = __activemask();
+    const float zcut = op == GE_S1 ? inv_c2 : 1.f;
+    if (!__any_sync(act, zr + tz[0] < zcut)) {
+      const float tau_c2 = tau * inv_c2;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float zeta = zr + tz[j], E = er * te[j];
+        const float rz = rcp_approx(zeta);   // 1 ulp: far below the route's TF32 / bf16 error
+        const float p1 = (1.f - E) * rz;
+        float out;
+        if (op == GE_RK1) {
+          out = E * w[j] + tau * p1 * v[j];
+        } else {
+          const float p2 = (1.f - p1) * rz;
+          if (op == GE_S2) {
+            out = w[j] + tau_c2 * p2 * v[j];
+          } else {
+            const float Ec = cr * tc[j];
+            out = Ec * w[j] + tau * (1.f - Ec) * rz * v[j];   // c2 tau phi1(-c2 zeta), c2 zeta >= 1
+            if (j < nv) o1[j * R] = E * w[j] + tau * (p1 - p2 * inv_c2) * v[j];
+          }
+        }
+        if (j < nv) o0[j * R] = out;
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const float zeta = zr + tz[j], E = er * te[j];
-      const float rz = rcp_approx(fmaxf(zeta, 1.f));   // 1 ulp: far below the route's TF32 / bf16 error
+      const float rz = rcp_approx(fmaxf(zeta, 1.f));
       float p1 = (1.f - E) * rz, p2 = (1.f - p1) * rz;
       const bool small = zeta < 1.f;
       if (__any_sync(act, small)) {
