@@ -38,7 +38,7 @@ typedef struct etd_plan_s* etd_plan;   /* opaque; owned by the library, released
 typedef enum {
   ETD_OK = 0,
   ETD_ERR_INVALID_ARG = 1,   /* a contract violation detected on the host; nothing was enqueued */
-  ETD_ERR_UNSUPPORTED = 2,   /* valid request this build cannot run (e.g. an axis length it has no kernel for) */
+  ETD_ERR_UNSUPPORTED = 2,   /* valid request the library cannot run (e.g. an axis length it has no kernel for) */
   ETD_ERR_CUDA = 3,          /* a CUDA runtime call failed; see etd_last_error() */
   ETD_ERR_OOM = 4,           /* device or pinned-host allocation failed */
   ETD_ERR_NONFINITE = 5,     /* etd_monitor found NaN/Inf values in the field */

@@ -21,7 +21,7 @@ Everything is FP64 NumPy/SciPy, written for readability, not speed:
 * ``sno``      the spectral neural operator used as the learned coarse propagator (forward pass,
                its chain-rule gradient, Adam) and the Parareal iteration.
 
-Readings of the paper taken here (each one is listed with its evidence in the design doc):
+Readings of the paper taken here:
 
 * the sine eigenvector matrix is used in its orthonormal form S = sqrt(2/N) P (Section 4 calls P
   orthogonal, but P P^T = (N/2) I);

@@ -1,7 +1,7 @@
 """The orthonormal DST-I along one axis, written from its definition (Section 4).
 
 S_ij = sqrt(2/N) sin(i j pi / N), i, j = 1..N-1 (the sine matrix P of Section 4 scaled to be
-orthonormal, reading c-1 in the design doc); S is symmetric and S S = I, so it is both the forward
+orthonormal: Section 4 calls P orthogonal, but P P^T = (N/2) I); S is symmetric and S S = I, so it is both the forward
 transform U~ = S^T (x)_a U and its inverse. Applied as a dense product along the axis.
 Parity: pinned (equals, up to sign, the numerically computed eigenvectors of A and B; S S = I).
 """

@@ -105,7 +105,8 @@ def _closed_form(N, h):
 @pytest.mark.parametrize("N,h", [(4, 0.25), (16, 1 / 16), (63, 0.01), (256, 1 / 256)])
 def test_eigenpairs_match_corrected_closed_form(N, h):
     """Section 4's simultaneous diagonalisation, with the squared sine in lambda^A and the
-    orthonormal sine matrix (readings c-1, c-2 in the design doc)."""
+    orthonormal sine matrix (Section 4 prints lambda^A without the square and calls the unscaled
+    sine matrix orthogonal)."""
     e = spectral.axis_eigen(N, h)
     lamA, lamB, mu, S = _closed_form(N, h)
     assert e.offdiag <= 1e-12 * np.max(np.abs(lamB))

@@ -174,7 +174,8 @@ def _table2_rows():
 @pytest.mark.parametrize("row", _table2_rows(), ids=lambda r: f"EIFE{r[0]}-NT{r[1]}")
 def test_table2_temporal_rows(row):
     """EIFE2 rows match at the printed N_T (c2 = 1/2); EIFE1 rows match at twice the printed N_T
-    (reading c-6 in the design doc: the printed EIFE1 labels are one row off)."""
+    (the printed EIFE1 row labels of Table 2 are one row off: the printed values are those of
+    twice the labelled N_T)."""
     scheme, nt, l2, h1 = row
     nt_run = nt if scheme == 2 else 2 * nt
     got_l2, got_h1 = _example51_reduced(scheme, nt_run)
