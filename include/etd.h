@@ -120,7 +120,9 @@ etd_status etd_run_host(etd_plan plan, void* u_host, int64_t nsteps, void* strea
 
 /* Apply the orthonormal DST-I S_a along paper axis `axis` (0 = x, 1 = y, 2 = z) to the dense device
  * field `in`, writing the dense device field `out` (may equal `in`). S_a is symmetric and its own
- * inverse, so this is both the forward transform U~ = S^T (x)_a U of Section 4 and its inverse. */
+ * inverse, so this is both the forward transform U~ = S^T (x)_a U of Section 4 and its inverse.
+ * Runs the FFT kernels of the plan's dtype on every route (a GEMM-route plan transforms with the FFT
+ * variant that ETD_ROUTE_AUTO would take). */
 etd_status etd_apply_dst(etd_plan plan, int axis, const void* in, void* out, void* stream);
 
 typedef struct {
@@ -192,7 +194,7 @@ etd_status etd_destroy(etd_plan plan);
  * (the batched kernel is a separate instantiation, so the compiler may contract and order the
  * floating-point operations differently; measured differences are at the dtype's rounding level).
  * Allocates per-problem fields and tables on the current device. Errors as for etd_plan_create;
- * count <= 0 is ETD_ERR_INVALID_ARG.
+ * count <= 0 is ETD_ERR_INVALID_ARG; the GEMM routes are ETD_ERR_UNSUPPORTED for batches.
  */
 typedef struct etd_batch_s* etd_batch;
 etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const double* h, const double* D,

@@ -121,3 +121,34 @@ def test_gemm_route_arguments_rejected_on_the_host(L):
     st, _ = _create(L, 2, (64, 64, 1), (1 / 64, 1 / 64, 1.0), opt=ctypes.byref(opt))
     assert st == nat.ETD_ERR_INVALID_ARG
     assert L.etd_status_string(nat.ETD_ERR_TIMEOUT) == b"a device wait ran out"
+
+
+def test_sno_and_parareal_arguments_rejected_on_the_host(L):
+    p = ctypes.c_void_p()
+    for args in [(7, 8, 4, 2, 4), (64, 0, 4, 2, 4), (64, 8, 64, 2, 4), (64, 8, 4, 0, 4), (64, 8, 4, 2, 0),
+                 (64, 300, 4, 2, 4), (64, 32, 4, 2, 4096)]:
+        assert L.etd_sno_create(ctypes.byref(p), *args) == nat.ETD_ERR_INVALID_ARG, args
+        assert not p.value
+    assert L.etd_sno_create(None, 64, 8, 4, 2, 4) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_sno_param_count(None) == 0
+    assert L.etd_sno_destroy(None) == nat.ETD_OK
+    D = (ctypes.c_double * 2)(1e-3, 1e-3)
+    assert L.etd_parareal_create(ctypes.byref(p), None, 64, 0, D, 0.01, 50, 4) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_parareal_create(ctypes.byref(p), None, 64, 2, D, 0.01, 50, 0) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_parareal_create(ctypes.byref(p), None, 64, 2, D, -1.0, 50, 4) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_parareal_run(None, None, None, 1, 0.0, 0.0, None, None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_parareal_destroy(None) == nat.ETD_OK
+
+
+def test_sno_parameter_layout_round_trips():
+    """The flat parameter layout of the binding matches the documented order and sizes."""
+    import numpy as np
+
+    from paper_2209_11922_gb300 import inputs, sno
+    w = inputs.SnoWorkload("t", N=16, C=3, M=2, L=2)
+    P = w.init_weights()
+    flat = sno.flatten(P)
+    assert flat.size == 2 * 3 + 3 + 2 * 2 * 2 * 3 * 3 + 2 * 3 * 3 + 2 * 3 + 3 + 1
+    back = sno.unflatten(flat, 3, 2, 2)
+    for k in sno.PARAM_NAMES:
+        assert np.allclose(back[k], np.asarray(P[k], dtype=np.float32)), k
