@@ -54,6 +54,12 @@ CASES = [
     ((64, 64, 64), 1e-3, 1e-2, 3, 2),
     ((32, 64, 96), 1e-3, 1e-2, 3, 2),
     ((96, 32, 64), 1e-3, 1e-2, 2, 1),
+    # extremes: the smallest axis (one 32-column K chunk, 32-wide tiles), the longest (K = 2048,
+    # 64 chunks, the full per-column tables), a single partial row tile
+    ((32, 32), 1e-2, 1e-2, 3, 2),
+    ((2048, 32), 1e-4, 5e-3, 2, 2),
+    ((32, 2048), 1e-4, 5e-3, 2, 2),
+    ((32, 32, 32), 1e-2, 1e-2, 2, 2),
 ]
 
 
