@@ -113,6 +113,22 @@ etd_status etd_run(etd_plan plan, void* u, int64_t nsteps, void* stream);
 /* One time step: etd_run(plan, u, 1, stream). */
 etd_status etd_step(etd_plan plan, void* u, void* stream);
 
+/* Time-dependent reaction (the scheme of Section 2 takes f = f(t, u); Example 5.1 of Section 5 is of
+ * this form): adds a separable source to the reaction,
+ *   f(t, u) = flin u + fcub u^3 + amp exp(-rate t) gx[i] gy[j] (gz[k]),
+ * gx, gy (and gz in 3D; NULL in 2D) HOST arrays of the N_a - 1 interior nodal values per axis,
+ * copied. The source enters where the reaction is spectral: its transform amp exp(-rate t)
+ * (S_x gx)(S_y gy)(S_z gz), evaluated at the stage times of the scheme (t_n for EIFE1 and the first
+ * EIFE2 stage, t_n + c2 tau for the second). All profiles NULL removes the source. Synchronous.
+ * Errors: ETD_ERR_INVALID_ARG (a missing or extra profile, non-finite values), ETD_ERR_UNSUPPORTED
+ * (GEMM routes). */
+etd_status etd_set_source(etd_plan plan, double amp, double rate, const double* gx, const double* gy,
+                          const double* gz);
+
+/* etd_run starting at time t0 (t_n = t0 + n tau; only a source set with etd_set_source depends on
+ * t). etd_run is etd_run_from with t0 = 0. */
+etd_status etd_run_from(etd_plan plan, void* u, int64_t nsteps, double t0, void* stream);
+
 /* Same as etd_run, but u_host is HOST memory (pinned or pageable) of the field's size: the call
  * copies it to a plan-owned device buffer, runs, copies the result back and synchronises the
  * stream before returning. */

@@ -48,6 +48,9 @@ _SIGS = {
                                 ctypes.POINTER(c_double), c_double, c_double, c_int, ctypes.POINTER(EtdOptions)]),
     "etd_run": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "etd_step": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "etd_run_from": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_void_p]),
+    "etd_set_source": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                               ctypes.POINTER(c_double)]),
     "etd_run_host": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "etd_apply_dst": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "etd_monitor": (c_int, [c_void_p, c_void_p, ctypes.POINTER(EtdMonitors), c_void_p]),

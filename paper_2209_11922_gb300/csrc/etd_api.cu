@@ -134,6 +134,10 @@ struct etd_plan_s {
   double* mon_out = nullptr;
   int mon_blocks = 0;
   size_t ws_bytes = 0;
+  bool src_on = false;        // separable time-dependent source set (2D, FFT routes)
+  void* src_tab = nullptr;    // gx [nx] then gy [ny] in the plan's dtype, index 0 = 0
+  void* clock = nullptr;      // unsigned long long steps completed, then double t0
+  double src_amp = 0, src_rate = 0;
   int gemm = 0;               // 0: FFT routes; 1 + GemmRoute: tensor-core transform passes
   void* gtab = nullptr;       // sine matrices S_a (fp32 TF32-rounded, or bf16 hi and lo)
   const void* gS[3][2] = {};  // per axis: S (TF32) or S_hi, S_lo (BF16x3)
@@ -263,6 +267,31 @@ etd_status launch(const Launch& L, cudaStream_t s) {
   cudaError_t e = cudaLaunchKernelExC(&cfg, L.fn, argv);
   if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return ETD_OK;
+}
+
+// Sets the source fields of the step's launches: the spectral passes (RK1 and S1 at t_n, S2 at
+// t_n + c2 tau) read the step count and start time; the first pass of a step advances the count.
+template <class T>
+void apply_source(etd_plan_s* pl) {
+  if (!pl->src_on || pl->step.empty()) return;
+  const T* tab = static_cast<const T*>(pl->src_tab);
+  const T* g[3] = {tab, tab + pl->nx, tab + pl->nx + pl->ny};
+  for (Launch& L : pl->step) {
+    PassArgs<T>* a = reinterpret_cast<PassArgs<T>*>(L.args);
+    if (a->op != OP_RK1 && a->op != OP_S1 && a->op != OP_S2) continue;
+    for (int d = 0; d < 3; ++d) a->src_g[d] = d < pl->ndim ? g[d] : nullptr;
+    a->step_ctr = static_cast<const unsigned long long*>(pl->clock);
+    a->src_t0 = reinterpret_cast<const double*>(static_cast<const char*>(pl->clock) + 8);
+    a->src_amp = pl->src_amp;
+    a->src_rate = pl->src_rate;
+    a->src_c = a->op == OP_S2 ? pl->opt.c2 : 0.0;
+  }
+  reinterpret_cast<PassArgs<T>*>(pl->step.front().args)->step_inc = static_cast<unsigned long long*>(pl->clock);
+}
+
+__global__ void source_clock_kernel(unsigned long long* steps, double* t0p, double t0) {
+  *steps = 0;
+  *t0p = t0;
 }
 
 template <class T>
@@ -1155,11 +1184,17 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   return ETD_OK;
 }
 
-etd_status etd_run(etd_plan pl, void* u, int64_t nsteps, void* stream) {
+etd_status etd_run_from(etd_plan pl, void* u, int64_t nsteps, double t0, void* stream) {
   if (!pl || !u) return fail(ETD_ERR_INVALID_ARG, "plan or u is NULL");
   if (nsteps < 0) return fail(ETD_ERR_INVALID_ARG, "nsteps < 0");
+  if (!std::isfinite(t0)) return fail(ETD_ERR_INVALID_ARG, "t0 must be finite");
   if (nsteps == 0) return ETD_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (pl->src_on) {
+    source_clock_kernel<<<1, 1, 0, s>>>(static_cast<unsigned long long*>(pl->clock),
+                                         reinterpret_cast<double*>(static_cast<char*>(pl->clock) + 8), t0);
+    ETD_CUDA(cudaGetLastError());
+  }
   std::vector<Launch> ent, ext;
   etd_status st = entry_exit_any(pl, true, u, ent);
   if (st != ETD_OK) return st;
@@ -1173,7 +1208,63 @@ etd_status etd_run(etd_plan pl, void* u, int64_t nsteps, void* stream) {
   return ETD_OK;
 }
 
+etd_status etd_run(etd_plan pl, void* u, int64_t nsteps, void* stream) {
+  return etd_run_from(pl, u, nsteps, 0.0, stream);
+}
+
 etd_status etd_step(etd_plan pl, void* u, void* stream) { return etd_run(pl, u, 1, stream); }
+
+etd_status etd_set_source(etd_plan pl, double amp, double rate, const double* gx, const double* gy,
+                          const double* gz) {
+  if (!pl) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+  if (!gx && !gy && !gz) {   // remove the source
+    if (!pl->src_on) return ETD_OK;
+    pl->src_on = false;
+  } else {
+    const double* g[3] = {gx, gy, gz};
+    for (int d = 0; d < pl->ndim; ++d)
+      if (!g[d]) return fail(ETD_ERR_INVALID_ARG, "one profile per axis is needed (axis %d is NULL)", d);
+    if (pl->ndim == 2 && gz) return fail(ETD_ERR_INVALID_ARG, "gz must be NULL for a 2D plan");
+    if (!std::isfinite(amp) || !std::isfinite(rate)) return fail(ETD_ERR_INVALID_ARG, "amp and rate must be finite");
+    if (pl->gemm) return fail(ETD_ERR_UNSUPPORTED, "sources are supported on the FFT routes");
+    const int n[3] = {pl->nx, pl->ny, pl->nz};
+    for (int d = 0; d < pl->ndim; ++d)
+      for (int i = 0; i < n[d] - 1; ++i)
+        if (!std::isfinite(g[d][i])) return fail(ETD_ERR_INVALID_ARG, "profile %d entry %d is not finite", d, i);
+    // spectral profiles S_a g_a (orthonormal DST-I, FP64, the product's index reduced mod 2N), index 0 = 0
+    const size_t tot = (size_t)pl->nx + pl->ny + pl->nz;
+    std::vector<double> h(tot, 0.0);
+    size_t off = 0;
+    for (int d = 0; d < pl->ndim; ++d) {
+      const long long N = n[d];
+      const double s0 = std::sqrt(2.0 / (double)N);
+      for (long long k = 1; k < N; ++k) {
+        double acc = 0.0;
+        for (long long j = 1; j < N; ++j) acc += g[d][j - 1] * std::sin(M_PI * (double)((j * k) % (2 * N)) / (double)N);
+        h[off + k] = s0 * acc;
+      }
+      off += n[d];
+    }
+    if (!pl->src_tab) ETD_CUDA(cudaMalloc(&pl->src_tab, tot * pl->elem));
+    if (!pl->clock) ETD_CUDA(cudaMalloc(&pl->clock, 16));
+    if (pl->elem == 4) {
+      std::vector<float> f(h.begin(), h.end());
+      ETD_CUDA(cudaMemcpy(pl->src_tab, f.data(), tot * 4, cudaMemcpyHostToDevice));
+    } else {
+      ETD_CUDA(cudaMemcpy(pl->src_tab, h.data(), tot * 8, cudaMemcpyHostToDevice));
+    }
+    ETD_CUDA(cudaMemset(pl->clock, 0, 16));
+    pl->src_on = true;
+    pl->src_amp = amp;
+    pl->src_rate = rate;
+  }
+  destroy_graph(pl);
+  etd_status st = pl->elem == 4 ? build_step<float>(pl) : build_step<double>(pl);
+  if (st != ETD_OK) return st;
+  if (pl->elem == 4) apply_source<float>(pl);
+  else apply_source<double>(pl);
+  return ETD_OK;
+}
 
 etd_status etd_run_host(etd_plan pl, void* u_host, int64_t nsteps, void* stream) {
   if (!pl || !u_host) return fail(ETD_ERR_INVALID_ARG, "plan or u_host is NULL");
@@ -1250,6 +1341,11 @@ etd_status etd_run_profiled(etd_plan pl, void* u, int64_t nsteps, void* stream, 
     ms[k] = 0;
     cnt[k] = 0;
   }
+  if (pl->src_on) {
+    source_clock_kernel<<<1, 1, 0, s>>>(static_cast<unsigned long long*>(pl->clock),
+                                         reinterpret_cast<double*>(static_cast<char*>(pl->clock) + 8), 0.0);
+    ETD_CUDA(cudaGetLastError());
+  }
   std::vector<Launch> all, ent, ext;
   etd_status st = entry_exit_any(pl, true, u, ent);
   if (st != ETD_OK) return st;
@@ -1309,6 +1405,8 @@ etd_status etd_destroy(etd_plan pl) {
   if (pl->host_dev) cudaFree(pl->host_dev);
   if (pl->mon_part) cudaFree(pl->mon_part);
   if (pl->gtab) cudaFree(pl->gtab);
+  if (pl->src_tab) cudaFree(pl->src_tab);
+  if (pl->clock) cudaFree(pl->clock);
   if (pl->dev_err) cudaFree(pl->dev_err);
   delete pl;
   return ETD_OK;

@@ -56,6 +56,14 @@ template <class T> struct PassArgs {
   const T* ex[3];   // exp(-tau D mu_a)
   const T* ec[3];   // exp(-c2 tau D mu_a)
   T sc, tau, c2, flin, fcub;
+  // Separable time-dependent source of the reaction, added where the reaction is spectral (the RK1,
+  // S1, S2 epilogues; src_g[0] == NULL: none): S f gains src_amp exp(-src_rate t) times the
+  // product of the per-axis spectral profiles src_g[a] = S_a g_a, at t = t0 + (steps - 1 + src_c) tau.
+  const T* src_g[3];                     // [n_a] per paper axis, index 0 (mode 0) = 0
+  const double* src_t0;                  // start time of the run
+  const unsigned long long* step_ctr;    // time steps begun in the run
+  unsigned long long* step_inc;          // the first pass of a step counts it (NULL: no)
+  double src_amp, src_rate, src_c;
 };
 
 // Asynchronous global -> shared copies (cp.async): every load of a tile is in flight at once and
@@ -78,6 +86,16 @@ template <> struct V2<double> { using type = double2; };
 template <class T, int N> constexpr int pass_min_blocks() {
   return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48)) ? 2 : 1;
 }
+// The first pass of a time step counts it, in CTA 0, after the dependency wait (the previous step's
+// passes, which read the count, have completed then). CTAs that return early (boundary tiles) call
+// this on their way out.
+template <class T> __device__ __forceinline__ void count_step(const PassArgs<T>& A) {
+  if (A.step_inc && blockIdx.x == 0 && threadIdx.x == 0) {
+    griddep_wait();
+    atomicAdd(A.step_inc, 1ULL);
+  }
+}
+
 template <class T, int N, bool ODD>
 __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) {
   using L = PairLayout<T, N, ODD>;
@@ -118,11 +136,17 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     if (A.axis == 1) {
       stride = A.nx;
       base = x0 + (long long)o * A.nx * A.ny;
-      if (A.ndim == 3 && o == 0) return;  // z = 0 plane: boundary, stays zero
+      if (A.ndim == 3 && o == 0) {         // z = 0 plane: boundary, stays zero
+        count_step(A);
+        return;
+      }
     } else {
       stride = A.nx * A.ny;
       base = x0 + (long long)o * A.nx;
-      if (o == 0) return;                  // y = 0 row: boundary, stays zero
+      if (o == 0) {                        // y = 0 row: boundary, stays zero
+        count_step(A);
+        return;
+      }
     }
   }
 
@@ -257,6 +281,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     }
   }
   griddep_wait();
+  if (A.step_inc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.step_inc, 1ULL);
   if (op == OP_ENTRY || op == OP_PACK) {
     load_dense(A.in0, b0);
   } else {
@@ -315,7 +340,14 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
     const T zjj = zj[j], ejj = ej[j];
     T out[2];
-    const T wv[2] = {w.x, w.y};
+    T wv[2] = {w.x, w.y};
+    if (A.src_g[0]) {   // the source's transform, added to the transformed reaction (rare path)
+      const double t = *A.src_t0 + ((double)*A.step_ctr - 1.0 + A.src_c) * (double)A.tau;
+      const double amp = A.src_amp * exp(-A.src_rate * t) * (double)A.src_g[A.axis][j] *
+                         (A.ndim == 3 ? (double)A.src_g[1][o] : 1.0);
+      wv[0] += (T)(amp * (double)A.src_g[0][x0 + 2 * p]);
+      wv[1] += (T)(amp * (double)A.src_g[0][x0 + 2 * p + 1]);
+    }
     // phi_k(-zeta) in closed form for zeta >= 1 from one reciprocal per mode; the series runs only
     // in warps holding a mode below zeta = 1 (or c2 zeta = 1), the low-mode corner of the spectrum
     // (every lane of the warp votes with its own predicate, so a lane that needs it gets it).

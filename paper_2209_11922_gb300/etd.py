@@ -82,9 +82,27 @@ class Plan:
         return ctypes.c_void_p(u.data_ptr())
 
     # ------------------------------------------------------------------ API
-    def run(self, u, nsteps: int, stream=None):
-        nat.check(nat.lib().etd_run(self._h, self._check_field(u), int(nsteps), _stream_ptr(stream)), "etd_run")
+    def run(self, u, nsteps: int, stream=None, t0: float = 0.0):
+        nat.check(nat.lib().etd_run_from(self._h, self._check_field(u), int(nsteps), float(t0), _stream_ptr(stream)),
+                  "etd_run_from")
         return u
+
+    def set_source(self, amp: float, rate: float, *profiles):
+        """Separable time-dependent source amp exp(-rate t) g_x[i] g_y[j] (g_z[k]) added to the reaction;
+        one profile of N_a - 1 interior values per axis (x first); no profiles removes it."""
+        L = nat.lib()
+        if not profiles or all(g is None for g in profiles):
+            nat.check(L.etd_set_source(self._h, 0.0, 0.0, None, None, None), "etd_set_source")
+            return
+        if len(profiles) != self.ndim:
+            raise ValueError("one profile per axis")
+        gs = [np.ascontiguousarray(g, dtype=np.float64) for g in profiles]
+        for a, g in enumerate(gs):
+            if g.shape != (self.N[a] - 1,):
+                raise ValueError(f"profile {a} must hold the N_{a} - 1 = {self.N[a] - 1} interior values")
+        P = ctypes.POINTER(ctypes.c_double)
+        ptrs = [g.ctypes.data_as(P) for g in gs] + [None] * (3 - self.ndim)
+        nat.check(L.etd_set_source(self._h, float(amp), float(rate), *ptrs), "etd_set_source")
 
     def step(self, u, stream=None):
         nat.check(nat.lib().etd_step(self._h, self._check_field(u), _stream_ptr(stream)), "etd_step")
