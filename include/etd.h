@@ -117,9 +117,9 @@ etd_status etd_step(etd_plan plan, void* u, void* stream);
  * this form): adds a separable source to the reaction,
  *   f(t, u) = flin u + fcub u^3 + amp exp(-rate t) gx[i] gy[j] (gz[k]),
  * gx, gy (and gz in 3D; NULL in 2D) HOST arrays of the N_a - 1 interior nodal values per axis,
- * copied. The source enters where the reaction is spectral: its transform amp exp(-rate t)
- * (S_x gx)(S_y gy)(S_z gz), evaluated at the stage times of the scheme (t_n for EIFE1 and the first
- * EIFE2 stage, t_n + c2 tau for the second). All profiles NULL removes the source. Synchronous.
+ * copied. The source joins the reaction in the pass that transforms it along x, as
+ * amp exp(-rate t) (S_x gx) gy (gz), evaluated at the stage times of the scheme (t_n for EIFE1 and
+ * the first EIFE2 stage, t_n + c2 tau for the second). All profiles NULL removes the source. Synchronous.
  * Errors: ETD_ERR_INVALID_ARG (a missing or extra profile, non-finite values), ETD_ERR_UNSUPPORTED
  * (GEMM routes). */
 etd_status etd_set_source(etd_plan plan, double amp, double rate, const double* gx, const double* gy,

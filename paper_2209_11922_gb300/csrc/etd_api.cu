@@ -269,24 +269,26 @@ etd_status launch(const Launch& L, cudaStream_t s) {
   return ETD_OK;
 }
 
-// Sets the source fields of the step's launches: the spectral passes (RK1 and S1 at t_n, S2 at
-// t_n + c2 tau) read the step count and start time; the first pass of a step advances the count.
+// Sets the source fields of the step's launches: the reaction passes (stage 1 at t_n, stage 2 at
+// t_n + c2 tau) read the step count and start time; the last pass of a step advances the count.
 template <class T>
 void apply_source(etd_plan_s* pl) {
   if (!pl->src_on || pl->step.empty()) return;
   const T* tab = static_cast<const T*>(pl->src_tab);
-  const T* g[3] = {tab, tab + pl->nx, tab + pl->nx + pl->ny};
+  int nreact = 0;
   for (Launch& L : pl->step) {
     PassArgs<T>* a = reinterpret_cast<PassArgs<T>*>(L.args);
-    if (a->op != OP_RK1 && a->op != OP_S1 && a->op != OP_S2) continue;
-    for (int d = 0; d < 3; ++d) a->src_g[d] = d < pl->ndim ? g[d] : nullptr;
+    if (a->op != OP_REACT) continue;
+    a->src_gx = tab;
+    a->src_gy = tab + pl->nx;
+    a->src_gz = pl->ndim == 3 ? tab + pl->nx + pl->ny : nullptr;
     a->step_ctr = static_cast<const unsigned long long*>(pl->clock);
     a->src_t0 = reinterpret_cast<const double*>(static_cast<const char*>(pl->clock) + 8);
     a->src_amp = pl->src_amp;
     a->src_rate = pl->src_rate;
-    a->src_c = a->op == OP_S2 ? pl->opt.c2 : 0.0;
+    a->src_c = nreact++ == 0 ? 0.0 : pl->opt.c2;
   }
-  reinterpret_cast<PassArgs<T>*>(pl->step.front().args)->step_inc = static_cast<unsigned long long*>(pl->clock);
+  reinterpret_cast<PassArgs<T>*>(pl->step.back().args)->step_inc = static_cast<unsigned long long*>(pl->clock);
 }
 
 __global__ void source_clock_kernel(unsigned long long* steps, double* t0p, double t0) {
@@ -1231,18 +1233,22 @@ etd_status etd_set_source(etd_plan pl, double amp, double rate, const double* gx
     for (int d = 0; d < pl->ndim; ++d)
       for (int i = 0; i < n[d] - 1; ++i)
         if (!std::isfinite(g[d][i])) return fail(ETD_ERR_INVALID_ARG, "profile %d entry %d is not finite", d, i);
-    // spectral profiles S_a g_a (orthonormal DST-I, FP64, the product's index reduced mod 2N), index 0 = 0
+    // x: the spectral profile S_x g_x (orthonormal DST-I, FP64, the product's index reduced mod 2N);
+    // y, z: the nodal profiles; index 0 (mode 0 / boundary node) = 0
     const size_t tot = (size_t)pl->nx + pl->ny + pl->nz;
     std::vector<double> h(tot, 0.0);
-    size_t off = 0;
-    for (int d = 0; d < pl->ndim; ++d) {
-      const long long N = n[d];
+    {
+      const long long N = n[0];
       const double s0 = std::sqrt(2.0 / (double)N);
       for (long long k = 1; k < N; ++k) {
         double acc = 0.0;
-        for (long long j = 1; j < N; ++j) acc += g[d][j - 1] * std::sin(M_PI * (double)((j * k) % (2 * N)) / (double)N);
-        h[off + k] = s0 * acc;
+        for (long long j = 1; j < N; ++j) acc += g[0][j - 1] * std::sin(M_PI * (double)((j * k) % (2 * N)) / (double)N);
+        h[k] = s0 * acc;
       }
+    }
+    size_t off = (size_t)n[0];
+    for (int d = 1; d < pl->ndim; ++d) {
+      for (int i = 1; i < n[d]; ++i) h[off + i] = g[d][i - 1];
       off += n[d];
     }
     if (!pl->src_tab) ETD_CUDA(cudaMalloc(&pl->src_tab, tot * pl->elem));

@@ -56,13 +56,15 @@ template <class T> struct PassArgs {
   const T* ex[3];   // exp(-tau D mu_a)
   const T* ec[3];   // exp(-c2 tau D mu_a)
   T sc, tau, c2, flin, fcub;
-  // Separable time-dependent source of the reaction, added where the reaction is spectral (the RK1,
-  // S1, S2 epilogues; src_g[0] == NULL: none): S f gains src_amp exp(-src_rate t) times the
-  // product of the per-axis spectral profiles src_g[a] = S_a g_a, at t = t0 + (steps - 1 + src_c) tau.
-  const T* src_g[3];                     // [n_a] per paper axis, index 0 (mode 0) = 0
+  // Separable time-dependent source of the reaction (REACT passes; src_gx == NULL: none). The pass
+  // stores S_x f(u), so it adds src_amp exp(-src_rate t) (S_x g_x)[k] g_y[y] g_z[z] at node row
+  // (y, z) and x mode k, t = t0 + (steps + src_c) tau.
+  const T* src_gx;                       // [nx] spectral x profile S_x g_x (mode 0 = 0)
+  const T* src_gy;                       // [ny] nodal y profile (boundary 0)
+  const T* src_gz;                       // [nz] nodal z profile (3D; NULL in 2D)
   const double* src_t0;                  // start time of the run
-  const unsigned long long* step_ctr;    // time steps begun in the run
-  unsigned long long* step_inc;          // the first pass of a step counts it (NULL: no)
+  const unsigned long long* step_ctr;    // time steps completed in the run
+  unsigned long long* step_inc;          // the last pass of a step counts it (NULL: no)
   double src_amp, src_rate, src_c;
 };
 
@@ -86,7 +88,7 @@ template <> struct V2<double> { using type = double2; };
 template <class T, int N> constexpr int pass_min_blocks() {
   return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48)) ? 2 : 1;
 }
-// The first pass of a time step counts it, in CTA 0, after the dependency wait (the previous step's
+// The last pass of a time step counts it, in CTA 0, after the dependency wait (the step's reaction
 // passes, which read the count, have completed then). CTAs that return early (boundary tiles) call
 // this on their way out.
 template <class T> __device__ __forceinline__ void count_step(const PassArgs<T>& A) {
@@ -340,14 +342,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
     const T zjj = zj[j], ejj = ej[j];
     T out[2];
-    T wv[2] = {w.x, w.y};
-    if (A.src_g[0]) {   // the source's transform, added to the transformed reaction (rare path)
-      const double t = *A.src_t0 + ((double)*A.step_ctr - 1.0 + A.src_c) * (double)A.tau;
-      const double amp = A.src_amp * exp(-A.src_rate * t) * (double)A.src_g[A.axis][j] *
-                         (A.ndim == 3 ? (double)A.src_g[1][o] : 1.0);
-      wv[0] += (T)(amp * (double)A.src_g[0][x0 + 2 * p]);
-      wv[1] += (T)(amp * (double)A.src_g[0][x0 + 2 * p + 1]);
-    }
+    const T wv[2] = {w.x, w.y};
     // phi_k(-zeta) in closed form for zeta >= 1 from one reciprocal per mode; the series runs only
     // in warps holding a mode below zeta = 1 (or c2 zeta = 1), the low-mode corner of the spectrum
     // (every lane of the warp votes with its own predicate, so a lane that needs it gets it).
@@ -441,6 +436,25 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
 
+  if (op == OP_REACT && A.src_gx) {
+    // separable source, already in the x-spectral form the pass stores (rare path)
+    const int q = q0 + p;
+    if (q < A.npairs) {
+      const double t = *A.src_t0 + ((double)*A.step_ctr + A.src_c) * (double)A.tau;
+      const double amp = A.src_amp * exp(-A.src_rate * t);
+      const int ra = 2 * q, rb = 2 * q + 1;
+      const double ga = amp * (double)A.src_gy[ra % A.ny] * (A.src_gz ? (double)A.src_gz[ra / A.ny] : 1.0);
+      const double gb = amp * (double)A.src_gy[rb % A.ny] * (A.src_gz ? (double)A.src_gz[rb / A.ny] : 1.0);
+      for (int j = l; j < N; j += TPP) {
+        const double g = (double)A.src_gx[j];
+        C v = b0p[L::at(j)];
+        v.x += (T)(ga * g);
+        v.y += (T)(gb * g);
+        b0p[L::at(j)] = v;
+      }
+    }
+    __syncthreads();
+  }
   griddep_launch_dependents();
   if (op == OP_EXIT) store_dense(b0, A.out0);
   else store_tile(b0, A.out0);
