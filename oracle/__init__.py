@@ -28,7 +28,12 @@ Readings of the paper taken here:
 * the reaction tensor F has entries from nodal values of f, i.e. F = M f(U) (group finite
   element reading of Section 4), so the spectral ODE is dU~/dt = -H (.) U~ + S f(S U~);
 * c2 = 1/2 in EIFE2 (Section 5);
-* u(0) is the given nodal field (the P_h u0 of eq. (2.5) is replaced by nodal data).
+* u(0) is the given nodal field (the P_h u0 of eq. (2.5) is replaced by nodal data);
+* periodic boundary conditions (Section 4, closing remarks): the printed eigenvalue formulas are
+  garbled; the eigenvalues are those of the circulant A = (h/6) circ(4, 1, .., 1) and
+  B = (1/h) G^P, lambda^A_i = (h/3)(2 + cos theta_i), lambda^B_i = (2/h)(1 - cos theta_i),
+  theta_i = 2 pi (i - 1)/N, pinned by the tests; the oracle itself diagonalises numerically;
+* Example 5.3's energy: the potential integral by nodal (lumped) quadrature.
 
 Parity status of each function is stated in its docstring; functions without an independent pin
 say "parity unpinned".

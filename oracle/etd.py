@@ -12,9 +12,13 @@ EIFE2, eq. (2.14), c_1 = 0, c_2 in (0, 1]:
     U~^{n+1} = e^{-tau H} U~^n + tau [(phi_1 - phi_2/c2)(-tau H) G~_1 + (phi_2/c2)(-tau H) G~_2]
 
 Every step starts from the physical nodal field and returns it, applying the transforms as dense
-products along each axis (no fusion, no FFT). Parity: pinned (dense matrix-exponential path on tiny
-grids, exact decay of a sine mode with f = 0, per-mode closed forms for linear f, the temporal
-orders of Theorems 3.1/3.2, the EIFE rows of Table 2).
+products along each axis (no fusion, no FFT). The periodic case (Section 4, closing remarks) is the
+same scheme on the circulant matrices' orthonormal eigenbasis (Section 4 applies it by a DFT per
+axis; here the basis is numerical, and the FFT form is a pin). Parity: pinned (dense
+matrix-exponential path on tiny grids, both boundary conditions; exact decay of a sine or Fourier
+mode with f = 0; per-mode closed forms for linear f; a constant periodic field following the scalar
+scheme with zero linear part; the temporal orders of Theorems 3.1/3.2; the EIFE rows of Table 2;
+the maximum bound and energy decay of Example 5.3).
 """
 from __future__ import annotations
 
@@ -58,6 +62,25 @@ def allen_cahn(flin: float = 1.0, fcub: float = -1.0) -> Reaction:
     return f
 
 
+def flory_huggins(theta: float, theta_c: float) -> Reaction:
+    """f(u) = (theta/2) ln((1 - u)/(1 + u)) + theta_c u, the Flory-Huggins reaction of Example 5.3
+    (Section 5.2), on nodal values; defined for |u| < 1."""
+    def f(t, u):
+        return 0.5 * theta * np.log((1.0 - u) / (1.0 + u)) + theta_c * u
+    return f
+
+
+def reaction(flin: float = 1.0, fcub: float = -1.0, flog: float = 0.0) -> Reaction:
+    """f(u) = flin u + fcub u^3 + flog * (1/2) ln((1 + u)/(1 - u)): the Allen-Cahn family plus a
+    logarithmic term (Flory-Huggins: flin = theta_c, fcub = 0, flog = -theta)."""
+    def f(t, u):
+        out = flin * u + fcub * u * u * u
+        if flog != 0.0:
+            out = out + flog * 0.5 * np.log((1.0 + u) / (1.0 - u))
+        return out
+    return f
+
+
 class Stepper:
     """EIFE1/EIFE2 on given per-axis orthonormal eigenvector matrices and per-mode rates H."""
 
@@ -94,15 +117,19 @@ class Stepper:
 
 
 def make_stepper(N: Sequence[int], h: Sequence[float], D: float, tau: float, scheme: int,
-                 c2: float = 0.5) -> Stepper:
-    """Assemble the 1D matrices per axis, diagonalise them, and build the stepper."""
-    eig = [axis_eigen(int(n), float(hh)) for n, hh in zip(N, h)]
+                 c2: float = 0.5, bc: str = "dirichlet") -> Stepper:
+    """Assemble the 1D matrices per axis (``bc`` 'dirichlet' or 'periodic'), diagonalise them, and
+    build the stepper. Periodic fields have N_a nodes per axis, Dirichlet fields N_a - 1."""
+    eig = [axis_eigen(int(n), float(hh), bc) for n, hh in zip(N, h)]
     H = mode_rates([e.mu for e in eig], D)
     return Stepper([e.P for e in eig], H, tau, scheme, c2)
 
 
 def run(u0: np.ndarray, N: Sequence[int], h: Sequence[float], D: float, tau: float, nsteps: int,
-        scheme: int = 2, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0) -> np.ndarray:
-    """``nsteps`` EIFE steps of u_t = D Lap u + flin u + fcub u^3 from nodal ``u0`` (float64)."""
-    st = make_stepper(N, h, D, tau, scheme, c2)
-    return st.run(np.asarray(u0, dtype=np.float64), nsteps, allen_cahn(flin, fcub))
+        scheme: int = 2, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0, bc: str = "dirichlet",
+        flog: float = 0.0) -> np.ndarray:
+    """``nsteps`` EIFE steps of u_t = D Lap u + f(u), f = flin u + fcub u^3 [+ flog atanh u], from
+    nodal ``u0`` (float64)."""
+    st = make_stepper(N, h, D, tau, scheme, c2, bc)
+    f = allen_cahn(flin, fcub) if flog == 0.0 else reaction(flin, fcub, flog)
+    return st.run(np.asarray(u0, dtype=np.float64), nsteps, f)

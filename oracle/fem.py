@@ -1,7 +1,9 @@
-"""Q1 (multilinear) finite elements on a uniform rectangular mesh, homogeneous Dirichlet.
+"""Q1 (multilinear) finite elements on a uniform rectangular mesh, homogeneous Dirichlet or periodic.
 
 Section 2.1: V_h is the tensor product of 1D continuous piecewise-linear spaces with nodes
 x^j = a + j h, j = 0..N, and only the N-1 interior hat functions kept (eq. (2.4)).
+Periodic case (Section 4, closing remarks): node N is node 0, so the N hat functions
+j = 0..N-1 are kept and element N-1 joins node N-1 to node 0.
 Section 4, eq. (4.1): the semi-discrete system is M dU/dt + K U = F with
 M = A_x (x) A_y (x) A_z, K = D (B_x (x) A_y (x) A_z + ...), A = (h/6) R, B = (1/h) G^D.
 
@@ -31,16 +33,34 @@ def element_stiffness_1d(h: float) -> np.ndarray:
     return np.array([[1.0 / h, -1.0 / h], [-1.0 / h, 1.0 / h]])
 
 
-def assemble_1d(N: int, h: float) -> tuple[np.ndarray, np.ndarray]:
-    """Assemble the 1D mass A and stiffness B over N elements; keep the N-1 interior nodes.
+def _check_bc(bc: str) -> None:
+    if bc not in ("dirichlet", "periodic"):
+        raise ValueError("bc must be 'dirichlet' or 'periodic'")
 
-    Returns dense (N-1) x (N-1) matrices. Node j of element e is e + j (j = 0, 1).
+
+def assemble_1d(N: int, h: float, bc: str = "dirichlet") -> tuple[np.ndarray, np.ndarray]:
+    """Assemble the 1D mass A and stiffness B over N elements.
+
+    Dirichlet: keep the N-1 interior nodes, dense (N-1) x (N-1). Node j of element e is e + j.
+    Periodic: node j of element e is (e + j) mod N, dense N x N (N >= 3, so that the two nodes of
+    an element are distinct and no element meets itself).
     """
-    if N < 2:
-        raise ValueError("need at least two intervals")
+    _check_bc(bc)
+    if N < 2 or (bc == "periodic" and N < 3):
+        raise ValueError("too few intervals")
+    me, ke = element_mass_1d(h), element_stiffness_1d(h)
+    if bc == "periodic":
+        A = np.zeros((N, N))
+        B = np.zeros((N, N))
+        for e in range(N):
+            nodes = (e, (e + 1) % N)
+            for a in range(2):
+                for b in range(2):
+                    A[nodes[a], nodes[b]] += me[a, b]
+                    B[nodes[a], nodes[b]] += ke[a, b]
+        return A, B
     Af = np.zeros((N + 1, N + 1))
     Bf = np.zeros((N + 1, N + 1))
-    me, ke = element_mass_1d(h), element_stiffness_1d(h)
     for e in range(N):
         for a in range(2):
             for b in range(2):
@@ -73,13 +93,34 @@ def element_matrices_nd(h: tuple, D: float) -> tuple[np.ndarray, np.ndarray]:
     return Me, Ke
 
 
-def assemble_global(N: tuple, h: tuple, D: float) -> tuple[sp.csr_matrix, sp.csr_matrix]:
-    """Assemble the global M and K over all Q1 elements; restrict to interior nodes.
+def assemble_global(N: tuple, h: tuple, D: float, bc: str = "dirichlet") -> tuple[sp.csr_matrix, sp.csr_matrix]:
+    """Assemble the global M and K over all Q1 elements.
 
-    N, h are per axis (x first). Interior unknowns are numbered x fastest, matching the array
-    layout (N_z-1, N_y-1, N_x-1) in C order.
+    N, h are per axis (x first). Dirichlet: restrict to interior nodes, numbered x fastest, matching
+    the array layout (N_z-1, N_y-1, N_x-1) in C order. Periodic: node indices wrap modulo N_a, and
+    the N_x N_y [N_z] unknowns match the layout (N_z, N_y, N_x).
     """
+    _check_bc(bc)
     d = len(N)
+    if bc == "periodic":
+        if min(N) < 3:
+            raise ValueError("too few intervals")
+        Me, Ke = element_matrices_nd(h, D)
+        strides = [int(np.prod(N[:a])) for a in range(d)]
+        rows, cols, mv, kv = [], [], [], []
+        locs = [tuple((n >> a) & 1 for a in range(d)) for n in range(2 ** d)]
+        for e in itertools.product(*[range(n) for n in reversed(N)]):
+            e = tuple(reversed(e))
+            nodes = [sum(((e[a] + lp[a]) % N[a]) * strides[a] for a in range(d)) for lp in locs]
+            for p in range(len(nodes)):
+                for q in range(len(nodes)):
+                    rows.append(nodes[p])
+                    cols.append(nodes[q])
+                    mv.append(Me[p, q])
+                    kv.append(Ke[p, q])
+        ntot = int(np.prod(N))
+        return (sp.coo_matrix((mv, (rows, cols)), shape=(ntot, ntot)).tocsr(),
+                sp.coo_matrix((kv, (rows, cols)), shape=(ntot, ntot)).tocsr())
     Me, Ke = element_matrices_nd(h, D)
     full = [n + 1 for n in N]
     strides = [int(np.prod(full[:a])) for a in range(d)]

@@ -7,7 +7,8 @@ Generator: SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom numb
 OOPSLA 2014). Element ``i`` of a stream with seed ``s`` is ``mix(s + (i + 1) * GAMMA)`` (mod 2**64),
 so the stream is counter-based and can be produced in any order. The top 53 bits map to [0, 1).
 Fields are filled in index order with x fastest, i.e. a C-ordered array of shape
-``(N_z - 1, N_y - 1, N_x - 1)`` (3D) or ``(N_y - 1, N_x - 1)`` (2D).
+``(N_z - 1, N_y - 1, N_x - 1)`` (3D) or ``(N_y - 1, N_x - 1)`` (2D); periodic fields keep every node,
+``(N_z, N_y, N_x)`` or ``(N_y, N_x)``.
 """
 from __future__ import annotations
 
@@ -50,9 +51,19 @@ def interior_shape(N: Sequence[int]) -> tuple:
     return tuple(int(n) - 1 for n in reversed(N))
 
 
+def field_shape(N: Sequence[int], bc: str = "dirichlet") -> tuple:
+    """Array shape of the nodal unknowns: interior nodes (Dirichlet) or all N_a nodes (periodic)."""
+    if bc == "periodic":
+        return tuple(int(n) for n in reversed(N))
+    if bc != "dirichlet":
+        raise ValueError("bc must be 'dirichlet' or 'periodic'")
+    return interior_shape(N)
+
+
 @dataclass(frozen=True)
 class Workload:
-    """One synthetic Allen-Cahn workload shaped like the paper's 2D/3D experiments."""
+    """One synthetic workload shaped like the paper's 2D/3D experiments: unit square/cube,
+    f(u) = flin u + fcub u^3 + flog atanh(u), boundary condition `bc`."""
 
     name: str
     N: tuple            # intervals per axis (N_x, N_y[, N_z]); unit domain -> h = 1/N
@@ -64,17 +75,25 @@ class Workload:
     u_hi: float
     seed: int = DEFAULT_SEED
     dtypes: tuple = field(default=("f64",))
+    bc: str = "dirichlet"
+    flin: float = 1.0
+    fcub: float = -1.0
+    flog: float = 0.0
 
     @property
     def h(self) -> tuple:
         return tuple(1.0 / n for n in self.N)
 
     @property
+    def shape(self) -> tuple:
+        return field_shape(self.N, self.bc)
+
+    @property
     def unknowns(self) -> int:
-        return int(np.prod(interior_shape(self.N)))
+        return int(np.prod(self.shape))
 
     def u0(self) -> np.ndarray:
-        return uniform_field(interior_shape(self.N), self.u_lo, self.u_hi, self.seed)
+        return uniform_field(self.shape, self.u_lo, self.u_hi, self.seed)
 
 
 # The synthetic workloads (unit square/cube, homogeneous Dirichlet, f = u - u^3).
@@ -87,7 +106,17 @@ AC3D_256 = Workload("allen_cahn_3d_256cubed_D1e-3_tau1e-2_etdrk2", (256, 256, 25
 AC3D_64 = Workload("allen_cahn_3d_64cubed_D1e-3_tau1e-2_etdrk2", (64, 64, 64), 1e-3, 1e-2, 500, 2,
                    -0.9, 0.9, DEFAULT_SEED + 2, ("f32", "f64"))
 
-WORKLOADS = {w.name: w for w in (AC2D_64, AC2D_1024, AC3D_256, AC3D_64)}
+# Grain coarsening with the Flory-Huggins reaction (Example 5.3, Section 5.2): periodic unit cube,
+# 128^3 mesh, eps = 0.01 (D = eps^2), theta = 0.8, theta_c = 1.6 (f = theta_c u - theta atanh u),
+# tau = T / N_T = 20 / 2048, u0 uniform(-0.9, 0.9) per node.
+GC3D_128 = Workload("grain_coarsening_3d_128cubed_periodic_flory_huggins_eps1e-2_tau5o512_etdrk2",
+                    (128, 128, 128), 1e-4, 20.0 / 2048, 2048, 2, -0.9, 0.9, DEFAULT_SEED + 6, ("f32", "f64"),
+                    "periodic", 1.6, 0.0, -0.8)
+GC3D_32 = Workload("grain_coarsening_3d_32cubed_periodic_flory_huggins_eps1e-2_tau5o512_etdrk2",
+                   (32, 32, 32), 1e-4, 20.0 / 2048, 64, 2, -0.9, 0.9, DEFAULT_SEED + 6, ("f32", "f64"),
+                   "periodic", 1.6, 0.0, -0.8)
+
+WORKLOADS = {w.name: w for w in (AC2D_64, AC2D_1024, AC3D_256, AC3D_64, GC3D_128, GC3D_32)}
 
 
 @dataclass(frozen=True)

@@ -60,3 +60,40 @@ def test_reaction_sign_error_is_caught(monkeypatch):
     monkeypatch.setattr(etd, "allen_cahn", lambda flin=1.0, fcub=-1.0: (lambda t, u: -flin * u + fcub * u ** 3))
     with pytest.raises(AssertionError):
         _dense_pin()
+
+
+# ---------------------------------------------------------------- periodic path and Flory-Huggins
+import test_oracle_periodic as periodic_pins
+from oracle import fem
+
+
+def test_periodic_pins_pass_unmutated():
+    periodic_pins.test_periodic_eigen_path_matches_dense_expm((4, 5), (0.25, 0.2), 2, "flory_huggins")
+    periodic_pins.test_periodic_step_matches_the_dft_route((16, 12), 2)
+
+
+def test_missing_wrap_element_is_caught(monkeypatch):
+    """Periodic assembly that forgets the element joining node N-1 to node 0."""
+    orig = fem.assemble_1d
+
+    def bad(N, h, bc="dirichlet"):
+        A, B = orig(N, h, bc)
+        if bc == "periodic":
+            A, B = A.copy(), B.copy()
+            me, ke = fem.element_mass_1d(h), fem.element_stiffness_1d(h)
+            for (i, j), (a, b) in zip([(N - 1, N - 1), (N - 1, 0), (0, N - 1), (0, 0)],
+                                      [(0, 0), (0, 1), (1, 0), (1, 1)]):
+                A[i, j] -= me[a, b]
+                B[i, j] -= ke[a, b]
+        return A, B
+    monkeypatch.setattr(fem, "assemble_1d", bad)
+    monkeypatch.setattr("oracle.spectral.assemble_1d", bad)
+    with pytest.raises(AssertionError):
+        periodic_pins.test_periodic_step_matches_the_dft_route((16, 12), 2)
+
+
+def test_flory_huggins_log_sign_error_is_caught(monkeypatch):
+    monkeypatch.setattr(etd, "flory_huggins", lambda th, thc: (
+        lambda t, u: 0.5 * th * np.log((1.0 + u) / (1.0 - u)) + thc * u))
+    with pytest.raises(AssertionError):
+        periodic_pins.test_periodic_eigen_path_matches_dense_expm((4, 5), (0.25, 0.2), 1, "flory_huggins")
