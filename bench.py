@@ -157,11 +157,9 @@ def run_reference(args, w):
     world, rank, _ = _dist_setup(args)
     if rank != 0:
         return 0
-    from oracle import etd as oetd
     sample = args.ref_sample_steps
     u0 = w.u0()
-    st = oetd.make_stepper(w.N, w.h, w.D, w.tau, w.scheme)
-    f = oetd.allen_cahn()
+    st, f = _oracle_stepper(w)
     for _ in range(args.warmup):
         st.run(u0, sample, f)
     t0 = time.perf_counter()
@@ -183,12 +181,18 @@ def run_reference(args, w):
     return 0
 
 
+def _oracle_stepper(w):
+    """The oracle's stepper and reaction for workload w (boundary condition and reaction included)."""
+    from oracle import etd as oetd
+    st = oetd.make_stepper(w.N, w.h, w.D, w.tau, w.scheme, 0.5, w.bc)
+    f = oetd.reaction(w.flin, w.fcub, w.flog) if w.flog else oetd.allen_cahn(w.flin, w.fcub)
+    return st, f
+
+
 def cpu_baseline(w, seconds: float = 15.0) -> dict:
     """Time the oracle on the host cores for a bounded sample of the same workload."""
-    from oracle import etd as oetd
     u0 = w.u0()
-    st = oetd.make_stepper(w.N, w.h, w.D, w.tau, w.scheme)
-    f = oetd.allen_cahn()
+    st, f = _oracle_stepper(w)
     t0 = time.perf_counter()
     st.run(u0, 1, f)
     one = time.perf_counter() - t0
@@ -214,7 +218,8 @@ def run_gb300(args, w):
     dtype = args.dtype
     tdt = torch.float32 if dtype == "f32" else torch.float64
     nsteps = args.time_steps or w.nsteps
-    plan = Plan(w.N, w.D, w.tau, scheme=w.scheme, dtype=dtype, route=args.route)
+    plan = Plan(w.N, w.D, w.tau, scheme=w.scheme, dtype=dtype, route=args.route, bc=w.bc, flin=w.flin,
+                fcub=w.fcub, flog=w.flog)
     info = plan.info()
     u0 = torch.from_numpy(w.u0().astype(np.float32 if dtype == "f32" else np.float64)).cuda()
     u = torch.empty_like(u0)
@@ -285,6 +290,7 @@ def run_gb300(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": w.name, "route": args.route, "mesh": list(w.N), "unknowns": w.unknowns, "time_steps_per_step": nsteps,
                        "D": w.D, "tau": w.tau, "scheme": "ETDRK2" if w.scheme == 2 else "ETDRK1",
+                       "bc": w.bc, "reaction": {"flin": w.flin, "fcub": w.fcub, "flog": w.flog},
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written between bench steps; within one run the fields stay L2-resident",
                        "kernels_per_time_step": info["kernels_per_step"],

@@ -2,8 +2,10 @@
  * etd.h - C ABI of the GB300 (sm_103a) exponential-integrator Q1 finite-element solver.
  *
  * Problem (Section 1, eq. (1.1); Section 2, eq. (2.1)): u_t = D Lap u + f(u) on a rectangle in 2D or
- * 3D with homogeneous Dirichlet data, f(u) = flin * u + fcub * u^3 (Allen-Cahn: flin = 1,
- * fcub = -1), applied to nodal values (the tensor F of Section 4 read as F = M f(U)).
+ * 3D with homogeneous Dirichlet data or periodic boundary conditions (Section 4, closing remarks),
+ * f(u) = flin u + fcub u^3 + flog artanh(u) (Allen-Cahn: flin = 1, fcub = -1, flog = 0; the
+ * Flory-Huggins reaction of Example 5.3, (theta/2) ln((1-u)/(1+u)) + theta_c u: flin = theta_c,
+ * fcub = 0, flog = -theta), applied to nodal values (the tensor F of Section 4 read as F = M f(U)).
  * Space: Q1 (multilinear) elements on a uniform mesh with N_a intervals of size h_a per axis
  * (Section 2.1); the unknowns are the (N_x-1)(N_y-1)[(N_z-1)] interior nodal values.
  * Time: one EIFE1 step, eq. (2.13) (ETDRK1), or one EIFE2 step, eq. (2.14) with c_1 = 0 and
@@ -12,10 +14,16 @@
  * S_a = sqrt(2/N_a) sin(i j pi / N_a), so each step is a forward DST-I along every axis, a per-mode
  * scaling by phi-functions of -tau D (mu_x,i + mu_y,j [+ mu_z,k]) with
  * mu_a,i = (6/h_a^2)(1 - cos(i pi/N_a))/(2 + cos(i pi/N_a)), and inverse DST-I along every axis.
+ * Periodic: A_a = (h_a/6) circ(4, 1, .., 1) and B_a = (1/h_a) G^P are circulant with eigenvalues
+ * depending on cos(2 pi i/N_a) only, so the orthonormal discrete Hartley transform
+ * H_a = N_a^{-1/2} cas(2 pi i j/N_a) (cas = cos + sin; symmetric, H^2 = I) diagonalises them and takes
+ * the place of the per-axis DFT / inverse DFT of Section 4, with
+ * mu_a,i = (6/h_a^2)(1 - cos(2 pi i/N_a))/(2 + cos(2 pi i/N_a)), i = 0..N_a-1.
  *
  * Conventions for every entry point:
  *  - A field `u` is the array of interior nodal values, x fastest (C order
- *    [N_z-1][N_y-1][N_x-1] or [N_y-1][N_x-1]), dense, element type per etd_options.dtype.
+ *    [N_z-1][N_y-1][N_x-1] or [N_y-1][N_x-1]), dense, element type per etd_options.dtype; on a
+ *    periodic plan every node 0..N_a-1 is an unknown ([N_z][N_y][N_x] or [N_y][N_x]).
  *  - Device pointers are CUDA device (or managed) memory owned by the caller; the plan never frees
  *    them. `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *  - Calls enqueue work asynchronously on `stream` unless stated; they return before the GPU work
@@ -57,7 +65,8 @@ typedef enum { ETD_F64 = 0, ETD_F32 = 1 } etd_dtype;            /* arithmetic an
  * ETD_ROUTE_AUTO: per axis, FP32 takes ETD_ROUTE_FFT for N >= 512 and ETD_ROUTE_FFT_HALF below;
  *   FP64 always takes the recurrence.
  * ETD_ROUTE_GEMM_TF32 and ETD_ROUTE_GEMM_BF16X3 (FP32 plans only; every N[a] a multiple of 32):
- *   the DST-I along an axis is the dense product with the N x N sine matrix S_a of Section 4,
+ *   the DST-I along an axis is the dense product with the N x N sine matrix S_a of Section 4 (periodic
+ *   plans: the N x N orthonormal Hartley matrix),
  *   computed on the tensor cores with FP32 accumulation and written transposed, so each pass
  *   contracts a contiguous axis. TF32: the field's values enter the product with TF32 precision
  *   (10 stored mantissa bits), S_a is rounded to TF32. BF16X3: both operands are split into bf16
@@ -76,15 +85,23 @@ typedef struct {
   etd_dtype dtype;   /* default ETD_F64 */
   etd_route route;   /* default ETD_ROUTE_AUTO (the DST-I by FFT kernels) */
   double c2;         /* EIFE2 stage node c_2 in (0, 1]; default 0.5 (Section 5) */
-  double flin;       /* f(u) = flin*u + fcub*u^3; defaults 1 and -1 (Allen-Cahn) */
+  double flin;       /* f(u) = flin*u + fcub*u^3 + flog*artanh(u); defaults 1, -1, 0 (Allen-Cahn) */
   double fcub;
   int debug;         /* default 0. ETD_DEBUG_STALL_FIRST_GEMM_PASS (GEMM routes): the first tensor-core
                         pass of every etd_run withholds its accumulator-ready signal, so that pass's
                         epilogue warps wait out their 2 s limit, abort and set the plan's error word;
                         the next synchronising call returns ETD_ERR_TIMEOUT and that run's field is
                         invalid. Tests the failure path; any other value is ignored. */
+  int bc;            /* boundary condition of every axis: ETD_BC_DIRICHLET (default) or ETD_BC_PERIODIC */
+  double flog;       /* coefficient of artanh(u) = (1/2) ln((1+u)/(1-u)) in f; default 0. Nonzero values
+                        run on periodic plans (any route) and on the GEMM routes; a Dirichlet plan on
+                        an FFT route and batches return ETD_ERR_UNSUPPORTED. Where it is nonzero the
+                        field must stay in (-1, 1) (|u| >= 1 gives non-finite values, which
+                        etd_monitor reports). */
 } etd_options;
 #define ETD_DEBUG_STALL_FIRST_GEMM_PASS 0x5A11
+#define ETD_BC_DIRICHLET 0
+#define ETD_BC_PERIODIC 1
 
 /* Fill *opt with the defaults above. Returns ETD_ERR_INVALID_ARG if opt is NULL. */
 etd_status etd_options_default(etd_options* opt);
@@ -95,11 +112,14 @@ etd_status etd_options_default(etd_options* opt);
  * Allocates the device workspace (five fields of N_x*N_y[*N_z] elements) and the FP64-derived
  * tables (eigenvalues mu_a, exp(-tau D mu_a), exp(-c2 tau D mu_a), twiddles) on the current
  * device, and uploads them. Supported N[a]: 2^k (4..2048) and 3*2^k (6..1536).
+ * Periodic plans (opt->bc = ETD_BC_PERIODIC) run the Hartley kernels on every FFT route (AUTO,
+ * FFT and FFT_HALF are the same there: one length-N complex FFT per pair of pencils), and the
+ * Hartley matrix on the GEMM routes.
  * opt may be NULL (defaults). On success *out receives the plan.
  * Errors: ETD_ERR_INVALID_ARG (out/N/h NULL, ndim not 2 or 3, N[a] < 2 or odd, h <= 0, D <= 0,
- * tau <= 0, c2 outside (0, 1], non-finite values, unknown route, a GEMM route with dtype
+ * tau <= 0, c2 outside (0, 1], non-finite values, unknown route or bc, a GEMM route with dtype
  * ETD_F64), ETD_ERR_UNSUPPORTED (N[a] without a kernel; a GEMM route with N[a] not a multiple of
- * 32), ETD_ERR_OOM, ETD_ERR_CUDA.
+ * 32; flog != 0 on a Dirichlet plan of an FFT route), ETD_ERR_OOM, ETD_ERR_CUDA.
  */
 etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const double* h, double D,
                            double tau, etd_scheme scheme, const etd_options* opt);
@@ -116,9 +136,10 @@ etd_status etd_step(etd_plan plan, void* u, void* stream);
 /* Time-dependent reaction (the scheme of Section 2 takes f = f(t, u); Example 5.1 of Section 5 is of
  * this form): adds a separable source to the reaction,
  *   f(t, u) = flin u + fcub u^3 + amp exp(-rate t) gx[i] gy[j] (gz[k]),
- * gx, gy (and gz in 3D; NULL in 2D) HOST arrays of the N_a - 1 interior nodal values per axis,
- * copied. The source joins the reaction in the pass that transforms it along x, as
- * amp exp(-rate t) (S_x gx) gy (gz), evaluated at the stage times of the scheme (t_n for EIFE1 and
+ * gx, gy (and gz in 3D; NULL in 2D) HOST arrays of the N_a - 1 interior nodal values per axis
+ * (periodic plans: the N_a nodal values), copied. The source joins the reaction in the pass that
+ * transforms it along x, as amp exp(-rate t) (S_x gx) gy (gz) (periodic: H_x gx), evaluated at the
+ * stage times of the scheme (t_n for EIFE1 and
  * the first EIFE2 stage, t_n + c2 tau for the second). All profiles NULL removes the source. Synchronous.
  * Errors: ETD_ERR_INVALID_ARG (a missing or extra profile, non-finite values), ETD_ERR_UNSUPPORTED
  * (GEMM routes). */
@@ -134,22 +155,28 @@ etd_status etd_run_from(etd_plan plan, void* u, int64_t nsteps, double t0, void*
  * stream before returning. */
 etd_status etd_run_host(etd_plan plan, void* u_host, int64_t nsteps, void* stream);
 
-/* Apply the orthonormal DST-I S_a along paper axis `axis` (0 = x, 1 = y, 2 = z) to the dense device
- * field `in`, writing the dense device field `out` (may equal `in`). S_a is symmetric and its own
- * inverse, so this is both the forward transform U~ = S^T (x)_a U of Section 4 and its inverse.
+/* Apply the orthonormal DST-I S_a (periodic plans: the orthonormal DHT H_a) along paper axis `axis`
+ * (0 = x, 1 = y, 2 = z) to the dense device field `in`, writing the dense device field `out` (may
+ * equal `in`). S_a and H_a are symmetric and their own inverses, so this is both the forward
+ * transform U~ = S^T (x)_a U of Section 4 and its inverse.
  * Runs the FFT kernels of the plan's dtype on every route (a GEMM-route plan transforms with the FFT
  * variant that ETD_ROUTE_AUTO would take). */
 etd_status etd_apply_dst(etd_plan plan, int axis, const void* in, void* out, void* stream);
 
 typedef struct {
   double mass;       /* 1^T M U with M the Q1 mass matrix */
-  double energy;     /* 1/2 U^T K U + sum_nodes prod(h) (u^2 - 1)^2 / 4 */
+  double energy;     /* 1/2 U^T K U + sum_nodes prod(h) G(u): G(u) = (u^2 - 1)^2 / 4 when flog = 0;
+                        otherwise the potential with G' = -f, G(0) = 0,
+                        G(u) = -flog (u artanh u + ln(1 - u^2)/2) - flin u^2/2 - fcub u^4/4, which for
+                        the Flory-Huggins coefficients is the energy density of Example 5.3,
+                        (theta/2)((1+u) ln(1+u) + (1-u) ln(1-u)) - (theta_c/2) u^2 */
   double maxabs;     /* max |u| */
   int64_t nonfinite; /* number of NaN/Inf values */
 } etd_monitors;
 
-/* FP64 reductions over the device field u; synchronises `stream` and writes *out.
- * Returns ETD_ERR_NONFINITE (with *out filled) when u holds NaN or Inf values. */
+/* FP64 reductions over the device field u (the plan's boundary condition and reaction); synchronises
+ * `stream` and writes *out. Returns ETD_ERR_NONFINITE (with *out filled) when u holds NaN or Inf
+ * values. */
 etd_status etd_monitor(etd_plan plan, const void* u, etd_monitors* out, void* stream);
 
 /* Kernel-level timing of one etd_run: records CUDA events around every kernel launch, runs
@@ -163,7 +190,7 @@ etd_status etd_run_profiled(etd_plan plan, void* u, int64_t nsteps, void* stream
 typedef struct {
   int ndim;
   int64_t N[3];
-  int64_t unknowns;            /* prod (N_a - 1) */
+  int64_t unknowns;            /* prod (N_a - 1); periodic: prod N_a */
   int64_t workspace_bytes;     /* device bytes owned by the plan */
   int kernels_per_step;        /* kernel launches per time step in etd_run */
   double bytes_per_step;       /* algorithmic HBM bytes per time step (field passes x size) */
@@ -182,7 +209,8 @@ const char* etd_pass_kind_name(int k);
  * allocation or a fixed memory budget, real-time loops where an allocation and the synchronisation
  * it may imply are not allowed, or a health check that must work before any plan exists).
  * Computes the same mass, energy, max|u| and non-finite count as etd_monitor for the dense device
- * field u (ndim in {2, 3}, N[a] intervals of size h[a] per axis, diffusion D, dtype) and writes
+ * field u (ndim in {2, 3}, N[a] intervals of size h[a] per axis, homogeneous Dirichlet, the
+ * Allen-Cahn potential (u^2 - 1)^2 / 4, diffusion D, dtype) and writes
  * them to out_dev, a DEVICE pointer to one etd_monitors, asynchronously on `stream`; it does not
  * synchronise and never returns ETD_ERR_NONFINITE (read out_dev->nonfinite instead).
  * Scratch: a fixed array inside this library (partial sums of one CTA per 2048 unknowns), present
@@ -210,7 +238,8 @@ etd_status etd_destroy(etd_plan plan);
  * (the batched kernel is a separate instantiation, so the compiler may contract and order the
  * floating-point operations differently; measured differences are at the dtype's rounding level).
  * Allocates per-problem fields and tables on the current device. Errors as for etd_plan_create;
- * count <= 0 is ETD_ERR_INVALID_ARG; the GEMM routes are ETD_ERR_UNSUPPORTED for batches.
+ * count <= 0 is ETD_ERR_INVALID_ARG; the GEMM routes and periodic boundaries are
+ * ETD_ERR_UNSUPPORTED for batches.
  */
 typedef struct etd_batch_s* etd_batch;
 etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const double* h, const double* D,

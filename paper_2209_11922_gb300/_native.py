@@ -21,6 +21,7 @@ ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD
 ETD_DEBUG_STALL_FIRST_GEMM_PASS = 0x5A11
 ETD_F64, ETD_F32 = 0, 1
 ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3 = 0, 1, 2, 3, 4
+ETD_BC_DIRICHLET, ETD_BC_PERIODIC = 0, 1
 ETD_NUM_PASS_KINDS = 8
 
 
@@ -30,7 +31,7 @@ class EtdPararealStats(ctypes.Structure):
 
 class EtdOptions(ctypes.Structure):
     _fields_ = [("dtype", c_int), ("route", c_int), ("c2", c_double), ("flin", c_double), ("fcub", c_double),
-                ("debug", c_int)]
+                ("debug", c_int), ("bc", c_int), ("flog", c_double)]
 
 
 class EtdMonitors(ctypes.Structure):

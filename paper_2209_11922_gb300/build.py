@@ -51,10 +51,10 @@ def generate() -> list:
     srcs = []
     decls, rows = [], []
     for tk, tn in TYPES.items():
-        for odd in ((True, False) if tk == "f32" else (False,)):
+        # transform variants (enum Variant of dst_engine.cuh): 1 odd extension (FP32 only),
+        # 0 half-length recurrence, 2 Hartley (periodic axes)
+        for v, o in ((("odd", 1), ("rec", 0), ("hart", 2)) if tk == "f32" else (("rec", 0), ("hart", 2))):
             for n in LENGTHS:
-                v = "odd" if odd else "rec"
-                o = "true" if odd else "false"
                 name = f"kinfo_{tk}_{v}_{n}"
                 path = os.path.join(GEN, f"inst_{tk}_{v}_{n}.cu")
                 _write_if_changed(path, (
@@ -71,10 +71,10 @@ def generate() -> list:
     _write_if_changed(reg, (
         '#include "pass_kernel.cuh"\n'
         "namespace etd {\n" + "\n".join(decls) + "\n"
-        "const KernelInfo* find_pass_kernel(int elem, int N, int odd) {\n"
+        "const KernelInfo* find_pass_kernel(int elem, int N, int variant) {\n"
         "  static const KernelInfo table[] = {\n" + "\n".join(rows) + "\n  };\n"
         "  for (const KernelInfo& k : table)\n"
-        "    if (k.elem == elem && k.N == N && k.odd == odd) return &k;\n"
+        "    if (k.elem == elem && k.N == N && k.odd == variant) return &k;\n"
         "  return nullptr;\n"
         "}\n"
         "}  // namespace etd\n"))

@@ -22,9 +22,21 @@
 //   The identities follow from splitting y into its even and odd parts about N/2. The prefix sum
 //   lets rounding grow like sqrt(N/2) eps, which FP64 absorbs and FP32 does not.
 //
+// HARTLEY (periodic axes, FP32 and FP64, M = N): the orthonormal discrete Hartley transform
+//     H_k = (1/sqrt(N)) sum_{j=0}^{N-1} x_j cas(2 pi j k / N),  cas t = cos t + sin t,  k = 0..N-1,
+//   which is symmetric and its own inverse, and diagonalises the circulant A and B of the periodic
+//   case because their eigenvalues depend on cos(2 pi k / N) only (modes k and N-k agree); it
+//   stands in for the DFT / inverse DFT pair of Section 4's remarks on periodic boundaries with
+//   real arithmetic throughout. The pair's length-N DFT Z (kernel exp(+2 pi i j k / N)) separates
+//   into the two real sequences' DFTs, A_k = (Z_k + conj Z_{N-k})/2 and
+//   B_k = (Z_k - conj Z_{N-k})/(2i), and H = Re + Im of each, so with z = Z_k, w = Z_{N-k}:
+//     H^a_k = sc (z.x + w.x + z.y - w.y),  H^b_k = sc (z.y + w.y + w.x - z.x),  sc = 1/(2 sqrt(N)).
+//   Every position 0..N-1 is data (no boundary slot).
+//
 // Layout: one pair occupies LP complex slots of shared memory; position j lives at
 // j + j / PADG (one padding slot every PADG entries) so that the strided writes of the first pass
-// hit distinct banks. Slot 0 holds position 0, which is the boundary node / mode 0 and is 0.
+// hit distinct banks. Slot 0 holds position 0, which for the sine variants is the boundary node /
+// mode 0 and is 0.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -162,6 +174,9 @@ __device__ __forceinline__ void Dft<T, R>::run(Cx<T>* x) {
 // plan is even so that the outputs k < N are exactly the butterfly outputs r < R/2.
 template <int... Rs> struct Radices {};
 template <class T, int N, bool ODD> struct FftPlan;
+// Transform variant of a kernel (template argument VAR): the two DST-I forms and the Hartley form.
+// The Hartley variant runs the recurrence variant's length-N FFT plan.
+enum Variant : int { V_REC = 0, V_ODD = 1, V_HART = 2 };
 #define ETD_PLAN(TYPE, NN, ODD_, TPP_, ...)                \
   template <> struct FftPlan<TYPE, NN, ODD_> {             \
     static constexpr bool ODD = ODD_;                      \
@@ -243,9 +258,10 @@ template <int NS, int R, int... Rest> struct TwSize<NS, R, Rest...> {
 template <class L> struct TwiddleCount;
 template <int... Rs> struct TwiddleCount<Radices<Rs...>> { static constexpr int value = TwSize<1, Rs...>::value; };
 
-template <class T, int N, bool ODD_> struct PairLayout {
-  using Plan = FftPlan<T, N, ODD_>;
+template <class T, int N, int VAR> struct PairLayout {
+  using Plan = FftPlan<T, N, VAR == V_ODD>;
   static constexpr bool ODD = Plan::ODD;
+  static constexpr bool HART = VAR == V_HART;
   static constexpr int M = Plan::M;
   static constexpr int TPP = Plan::TPP;
   static constexpr int PADG = FirstRadix<typename Plan::R>::value;
@@ -265,7 +281,9 @@ template <class T, int N, bool ODD_> struct PairLayout {
 // (jj/Ns)*Ns*R + (jj mod Ns) + r*Ns. In place: all reads, barrier, all writes, barrier.
 // The first pass folds in the input map of the variant (odd extension or the y_j of the
 // recurrence); the last pass of the ODD variant writes only k < N, already scaled by -i sc.
-// Nodal reaction f(u) = flin u + fcub u^3 applied to both packed pencils.
+// Nodal reaction f(u) = flin u + fcub u^3 applied to both packed pencils as the first pass reads
+// them (the logarithmic term of the Flory-Huggins reaction is applied by the pass kernel itself,
+// outside the butterfly code).
 template <class T> struct React {
   bool on;
   T flin, fcub;
@@ -274,12 +292,12 @@ template <class T> struct React {
   }
 };
 
-template <class T, int N, bool ODD, int NB, int NS, bool FIRST, int R, int... Rest>
+template <class T, int N, int VAR, int NB, int NS, bool FIRST, int R, int... Rest>
 __device__ __forceinline__ void stockham(Cx<T>* const (&bps)[NB], const Cx<T>* __restrict__ tw,
                                          const T* __restrict__ sn, int l, T sc, React<T> rx) {
   // tw points at this pass's table (unused when NS == 1); the first pass applies rx to its input.
   // NB independent pairs (one per buffer) go through the pass together, sharing its barriers.
-  using L = PairLayout<T, N, ODD>;
+  using L = PairLayout<T, N, VAR>;
   constexpr int M = L::M;
   constexpr int TPP = L::TPP;
   constexpr int TP = M / R;
@@ -306,6 +324,8 @@ __device__ __forceinline__ void stockham(Cx<T>* const (&bps)[NB], const Cx<T>* _
               const Cx<T> c = rx(bp[L::at(M - idx)]);
               xv = {-c.x, -c.y};
             }
+          } else if constexpr (FIRST && L::HART) {
+            xv = rx(bp[L::at(idx)]);
           } else if constexpr (FIRST) {
             if (idx == 0) {
               xv = {T(0), T(0)};
@@ -350,13 +370,13 @@ __device__ __forceinline__ void stockham(Cx<T>* const (&bps)[NB], const Cx<T>* _
   }
   __syncthreads();
   if constexpr (!LAST)
-    stockham<T, N, ODD, NB, NS * R, false, Rest...>(bps, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc, rx);
+    stockham<T, N, VAR, NB, NS * R, false, Rest...>(bps, tw + (NS > 1 ? (R - 1) * NS : 0), sn, l, sc, rx);
 }
 
-template <class T, int N, bool ODD, int NB, int... Rs>
+template <class T, int N, int VAR, int NB, int... Rs>
 __device__ __forceinline__ void run_fft(Cx<T>* const (&bps)[NB], const Cx<T>* tw, const T* sn, int l, T sc,
                                         React<T> rx, Radices<Rs...>) {
-  stockham<T, N, ODD, NB, 1, true, Rs...>(bps, tw, sn, l, sc, rx);
+  stockham<T, N, VAR, NB, 1, true, Rs...>(bps, tw, sn, l, sc, rx);
 }
 
 // `mask` names the lanes of the warp that exist (a CTA may have fewer than 32 threads).
@@ -365,19 +385,40 @@ __device__ __forceinline__ Cx<T> shfl_up_cx(unsigned mask, Cx<T> v, int d, int w
   return {__shfl_up_sync(mask, v.x, d, width), __shfl_up_sync(mask, v.y, d, width)};
 }
 
-// Full orthonormal DST-I of NB independent pairs (one per buffer bps[b]), in place: on return
-// positions 0..N-1 of each hold the result (position 0 = 0). sc = sqrt(2/N)/2. tw holds the
+// Full orthonormal DST-I (Hartley variant: DHT) of NB independent pairs (one per buffer bps[b]), in
+// place: on return positions 0..N-1 of each hold the result (DST: position 0 = 0). sc = sqrt(2/N)/2
+// (DHT: 1/(2 sqrt(N))). tw holds the
 // per-pass twiddle tables, sn = sin(pi j / N) (recurrence only). scrs[b] is shared scratch of
 // TPP/32 complex per pair (recurrence, TPP > 32). With rx.on the input is first mapped through the
 // nodal reaction (fused into the first pass). Running two transforms together halves the number
 // of barrier-separated phases they cost.
-template <class T, int N, bool ODD, int NB>
+template <class T, int N, int VAR, int NB>
 __device__ __forceinline__ void dst_pairs(Cx<T>* const (&bps)[NB], const Cx<T>* __restrict__ tw,
                                           const T* __restrict__ sn, int l, Cx<T>* const (&scrs)[NB], T sc,
                                           React<T> rx = React<T>{false, T(0), T(0)}) {
-  using L = PairLayout<T, N, ODD>;
-  run_fft<T, N, ODD, NB>(bps, tw, sn, l, sc, rx, typename FftPlan<T, N, ODD>::R{});
-  if constexpr (!L::ODD) {
+  using L = PairLayout<T, N, VAR>;
+  run_fft<T, N, VAR, NB>(bps, tw, sn, l, sc, rx, typename L::Plan::R{});
+  if constexpr (L::HART) {
+    // each thread owns the position pairs (k, N-k), k = l, l + TPP, .. <= N/2: no barrier between
+    // its reads and writes
+    constexpr int TPP = L::TPP;
+    constexpr int C = (N / 2 + 1 + TPP - 1) / TPP;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      Cx<T>* __restrict__ bp = bps[b];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int k = l + i * TPP;
+        if (k <= N / 2) {
+          const int m = k == 0 ? 0 : N - k;
+          const Cx<T> z = bp[L::at(k)], w = bp[L::at(m)];
+          bp[L::at(k)] = Cx<T>{sc * (z.x + w.x + z.y - w.y), sc * (z.y + w.y + w.x - z.x)};
+          if (m != k) bp[L::at(m)] = Cx<T>{sc * (w.x + z.x + w.y - z.y), sc * (w.y + z.y + z.x - w.x)};
+        }
+      }
+    }
+    __syncthreads();
+  } else if constexpr (!L::ODD) {
     constexpr int TPP = L::TPP;
     constexpr int C = (N / 2) / TPP;
     static_assert(C * TPP == N / 2, "N/2 must be a multiple of the threads per pair");
@@ -440,19 +481,19 @@ __device__ __forceinline__ void dst_pairs(Cx<T>* const (&bps)[NB], const Cx<T>* 
   }
 }
 
-template <class T, int N, bool ODD>
+template <class T, int N, int VAR>
 __device__ __forceinline__ void dst_pair(Cx<T>* bp, const Cx<T>* __restrict__ tw, const T* __restrict__ sn, int l,
                                          Cx<T>* scr, T sc, React<T> rx = React<T>{false, T(0), T(0)}) {
   Cx<T>* const bps[1] = {bp};
   Cx<T>* const scrs[1] = {scr};
-  dst_pairs<T, N, ODD, 1>(bps, tw, sn, l, scrs, sc, rx);
+  dst_pairs<T, N, VAR, 1>(bps, tw, sn, l, scrs, sc, rx);
 }
 
 // Pointwise epilogue over positions 0..N-1 of one pair: bp[j] = epi(j, bp[j]). The loop is kept
 // rolled so that the epilogue's code appears once in the kernel.
-template <class T, int N, bool ODD, class Epi>
+template <class T, int N, int VAR, class Epi>
 __device__ __forceinline__ void epilogue_pair(Cx<T>* __restrict__ bp, int l, Epi&& epi) {
-  using L = PairLayout<T, N, ODD>;
+  using L = PairLayout<T, N, VAR>;
 #pragma unroll 1
   for (int j = l; j < N; j += L::TPP) bp[L::at(j)] = epi(j, bp[L::at(j)]);
   __syncthreads();

@@ -36,7 +36,7 @@
 
 namespace etd {
 // registry of instantiated pass kernels (generated per (type, N) translation units)
-const KernelInfo* find_pass_kernel(int elem, int N, int odd);
+const KernelInfo* find_pass_kernel(int elem, int N, int variant);
 // tensor-core transform passes (gemm_inst.cu)
 const GemmKernelInfo* find_gemm_kernel(int bn, int route);
 }  // namespace etd
@@ -109,10 +109,11 @@ struct etd_plan_s {
   int scheme = 2;
   etd_options opt{};
   int elem = 8;
-  int odd[3] = {0, 0, 0};  // DST variant per axis: 1 odd extension, 0 half-length recurrence
+  int odd[3] = {0, 0, 0};  // transform variant per axis: V_ODD, V_REC (DST-I) or V_HART (periodic)
+  int periodic = 0;        // every axis periodic (Hartley kernels), else homogeneous Dirichlet
   int nx = 1, ny = 1, nz = 1;
   size_t nfield = 0;       // pitched elements per field
-  int64_t unknowns = 0;    // interior unknowns
+  int64_t unknowns = 0;    // unknowns (interior nodes; periodic: all nodes)
   int device = 0;
   int num_sms = 148;
   void* ws = nullptr;      // fields
@@ -134,12 +135,12 @@ struct etd_plan_s {
   double* mon_out = nullptr;
   int mon_blocks = 0;
   size_t ws_bytes = 0;
-  bool src_on = false;        // separable time-dependent source set (2D, FFT routes)
-  void* src_tab = nullptr;    // gx [nx] then gy [ny] in the plan's dtype, index 0 = 0
+  bool src_on = false;        // separable time-dependent source set (FFT routes)
+  void* src_tab = nullptr;    // gx [nx], gy [ny] (, gz [nz]) in the plan's dtype; Dirichlet: index 0 = 0
   void* clock = nullptr;      // unsigned long long steps completed, then double t0
   double src_amp = 0, src_rate = 0;
   int gemm = 0;               // 0: FFT routes; 1 + GemmRoute: tensor-core transform passes
-  void* gtab = nullptr;       // sine matrices S_a (fp32 TF32-rounded, or bf16 hi and lo)
+  void* gtab = nullptr;       // sine (periodic: Hartley) matrices S_a (fp32 TF32-rounded, or bf16 hi and lo)
   const void* gS[3][2] = {};  // per axis: S (TF32) or S_hi, S_lo (BF16x3)
   int* dev_err = nullptr;     // set by a tensor-core pass whose wait ran out
 };
@@ -163,6 +164,7 @@ void fill_common(const etd_plan_s* pl, PassArgs<T>& a) {
   a.c2 = (T)pl->opt.c2;
   a.flin = (T)pl->opt.flin;
   a.fcub = (T)pl->opt.fcub;
+  a.flog = (T)pl->opt.flog;
 }
 
 // Build one pass launch. fields are indices into F (or -1 for a user pointer given later).
@@ -430,7 +432,8 @@ uint16_t round_bf16(double v, double* back) {
   return h;
 }
 
-// S_a[j][k] = sqrt(2/N) sin(pi (j k mod 2N) / N), j, k < N, in FP64, stored per axis in the operand
+// S_a[j][k] = sqrt(2/N) sin(pi (j k mod 2N) / N) (periodic: N^{-1/2} cas(2 pi (j k mod N) / N)), j, k < N,
+// in FP64, stored per axis in the operand
 // format of the route: fp32 rounded to TF32, or bf16 hi = rn(S), lo = rn(S - hi).
 etd_status upload_gemm_tables(etd_plan_s* pl) {
   size_t offs[3][2], total = 0;
@@ -445,10 +448,16 @@ etd_status upload_gemm_tables(etd_plan_s* pl) {
   std::vector<unsigned char> h(total, 0);
   for (int a = 0; a < pl->ndim; ++a) {
     const long long n = pl->N[a];
-    const double s0 = sqrt(2.0 / (double)n);
+    const double s0 = pl->periodic ? 1.0 / sqrt((double)n) : sqrt(2.0 / (double)n);
     for (long long j = 0; j < n; ++j)
       for (long long k = 0; k < n; ++k) {
-        const double v = s0 * sin(M_PI * (double)((j * k) % (2 * n)) / (double)n);
+        double v;
+        if (pl->periodic) {   // Hartley: cas(2 pi j k / n), j k reduced mod n
+          const double t = 2.0 * M_PI * (double)((j * k) % n) / (double)n;
+          v = s0 * (cos(t) + sin(t));
+        } else {
+          v = s0 * sin(M_PI * (double)((j * k) % (2 * n)) / (double)n);
+        }
         const size_t e = (size_t)(j * n + k);
         if (!split) {
           const float f = round_tf32(v);
@@ -536,6 +545,7 @@ etd_status make_gemm_launch(etd_plan_s* pl, int a, const void* in, const void* i
   g.c2 = (float)pl->opt.c2;
   g.flin = (float)pl->opt.flin;
   g.fcub = (float)pl->opt.fcub;
+  g.flog = (float)pl->opt.flog;
   g.err = pl->dev_err;
   g.stall = stall ? 1 : 0;
   L.fn = k->fn;
@@ -633,11 +643,12 @@ etd_status entry_exit_any(etd_plan_s* pl, bool entry, void* u, std::vector<Launc
 // FP64 on the host, rounded once to T, appended to h for one axis of length n: the per-pass twiddle
 // tables (pass with NS > 1 and radix R holds exp(2 pi i k r / (NS R)) at [(r-1)*NS + k], k < NS,
 // r = 1..R-1, the layout the Stockham passes read), sin(pi j / n), and per mode i the values
-// zeta = tau D mu_i, exp(-zeta), exp(-c2 zeta) with mu_i = (6/h^2)(1 - cos)/(2 + cos) of theta = i pi / n.
+// zeta = tau D mu_i, exp(-zeta), exp(-c2 zeta) with mu_i = (6/h^2)(1 - cos)/(2 + cos) of theta = i pi / n
+// (periodic axes: theta = 2 pi i / n, mode 0 included with zeta = 0).
 // offs receives the five table starts (element offsets into h).
 template <class T>
 void append_axis_tables(const KernelInfo* k, int n, double hh, double tauD, double c2, std::vector<T>& h,
-                        size_t offs[5]) {
+                        size_t offs[5], bool periodic = false) {
   offs[0] = h.size();
   int NS = 1;
   size_t t = 0;
@@ -667,7 +678,7 @@ void append_axis_tables(const KernelInfo* k, int n, double hh, double tauD, doub
   for (int i = 0; i < n; ++i) {
     double zeta = 0.0;
     if (i > 0) {
-      const double th = M_PI * (double)i / (double)n;
+      const double th = (periodic ? 2.0 * M_PI : M_PI) * (double)i / (double)n;
       const double s = sin(0.5 * th);
       const double mu = 12.0 / (hh * hh) * s * s / (2.0 + cos(th));  // (6/h^2)(1-cos)/(2+cos)
       zeta = tauD * mu;
@@ -685,8 +696,8 @@ etd_status upload_tables(etd_plan_s* pl) {
   for (int a = 0; a < pl->ndim; ++a) {
     const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a], pl->odd[a]);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %lld", (long long)pl->N[a]);
-    append_axis_tables<T>(k, (int)pl->N[a], pl->h[a], pl->tau * pl->D, pl->opt.c2, h, offs[a]);
-    pl->sc[a] = 0.5 * sqrt(2.0 / (double)pl->N[a]);
+    append_axis_tables<T>(k, (int)pl->N[a], pl->h[a], pl->tau * pl->D, pl->opt.c2, h, offs[a], pl->periodic != 0);
+    pl->sc[a] = pl->periodic ? 0.5 / sqrt((double)pl->N[a]) : 0.5 * sqrt(2.0 / (double)pl->N[a]);
   }
   ETD_CUDA(cudaMalloc(&pl->tables, h.size() * sizeof(T)));
   ETD_CUDA(cudaMemcpy(pl->tables, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -825,6 +836,7 @@ int batch_args(const etd_batch_s* b, const std::vector<BatchTables>& tabs, int i
   a.c2 = (T)b->opt.c2;
   a.flin = (T)b->opt.flin;
   a.fcub = (T)b->opt.fcub;
+  a.flog = (T)b->opt.flog;
   a.op = op;
   a.axis = axis;
   T* F = static_cast<T*>(b->ws) + b->field_off[i];
@@ -1091,6 +1103,8 @@ etd_status etd_options_default(etd_options* opt) {
   opt->flin = 1.0;
   opt->fcub = -1.0;
   opt->debug = 0;
+  opt->bc = ETD_BC_DIRICHLET;
+  opt->flog = 0.0;
   return ETD_OK;
 }
 
@@ -1108,11 +1122,13 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   etd_options_default(&o);
   if (opt) o = *opt;
   if (!(std::isfinite(o.c2) && o.c2 > 0 && o.c2 <= 1)) return fail(ETD_ERR_INVALID_ARG, "c2 must lie in (0, 1]");
-  if (!std::isfinite(o.flin) || !std::isfinite(o.fcub)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
+  if (!std::isfinite(o.flin) || !std::isfinite(o.fcub) || !std::isfinite(o.flog))
+    return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
   if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
   if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF &&
       o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3)
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
+  if (o.bc != ETD_BC_DIRICHLET && o.bc != ETD_BC_PERIODIC) return fail(ETD_ERR_INVALID_ARG, "unknown boundary condition");
   const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
   if (gemm && o.dtype != ETD_F32) return fail(ETD_ERR_INVALID_ARG, "the GEMM routes compute in FP32 (dtype ETD_F32)");
   for (int a = 0; a < ndim; ++a) {
@@ -1128,7 +1144,10 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
     for (int a = 0; a < ndim; ++a)
       if (N[a] % 32)
         return fail(ETD_ERR_UNSUPPORTED, "N[%d] = %lld: the GEMM routes need multiples of 32", a, (long long)N[a]);
+  if (o.flog != 0.0 && !gemm && o.bc != ETD_BC_PERIODIC)
+    return fail(ETD_ERR_UNSUPPORTED, "the artanh reaction term runs on periodic plans and on the GEMM routes");
   etd_plan_s* pl = new etd_plan_s();
+  pl->periodic = o.bc == ETD_BC_PERIODIC;
   pl->ndim = ndim;
   for (int a = 0; a < ndim; ++a) {
     pl->N[a] = N[a];
@@ -1142,15 +1161,18 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   for (int a = 0; a < ndim; ++a) {
     // FP32: the odd extension keeps rounding at log N; AUTO uses it from N = 512 up and the
     // half-length recurrence (sqrt(N/2) eps <= 11 eps) below, where it is twice as fast.
-    if (o.dtype != ETD_F32 || o.route == ETD_ROUTE_FFT_HALF) pl->odd[a] = 0;
-    else if (o.route == ETD_ROUTE_FFT) pl->odd[a] = 1;
-    else pl->odd[a] = N[a] >= 512 ? 1 : 0;
+    // Periodic axes: the Hartley variant (a plain length-N FFT, rounding like log N) on every route.
+    if (pl->periodic) pl->odd[a] = V_HART;
+    else if (o.dtype != ETD_F32 || o.route == ETD_ROUTE_FFT_HALF) pl->odd[a] = V_REC;
+    else if (o.route == ETD_ROUTE_FFT) pl->odd[a] = V_ODD;
+    else pl->odd[a] = N[a] >= 512 ? V_ODD : V_REC;
   }
   pl->nx = (int)N[0];
   pl->ny = (int)N[1];
   pl->nz = ndim == 3 ? (int)N[2] : 1;
   pl->nfield = (size_t)pl->nx * pl->ny * pl->nz;
-  pl->unknowns = (N[0] - 1) * (N[1] - 1) * (ndim == 3 ? N[2] - 1 : 1);
+  const int64_t cut = pl->periodic ? 0 : 1;
+  pl->unknowns = (N[0] - cut) * (N[1] - cut) * (ndim == 3 ? N[2] - cut : 1);
   auto bail = [&](etd_status s) {
     etd_destroy(pl);
     return s;
@@ -1230,25 +1252,38 @@ etd_status etd_set_source(etd_plan pl, double amp, double rate, const double* gx
     if (!std::isfinite(amp) || !std::isfinite(rate)) return fail(ETD_ERR_INVALID_ARG, "amp and rate must be finite");
     if (pl->gemm) return fail(ETD_ERR_UNSUPPORTED, "sources are supported on the FFT routes");
     const int n[3] = {pl->nx, pl->ny, pl->nz};
+    const int cut = pl->periodic ? 0 : 1;   // profile entries per axis: n - cut
     for (int d = 0; d < pl->ndim; ++d)
-      for (int i = 0; i < n[d] - 1; ++i)
+      for (int i = 0; i < n[d] - cut; ++i)
         if (!std::isfinite(g[d][i])) return fail(ETD_ERR_INVALID_ARG, "profile %d entry %d is not finite", d, i);
-    // x: the spectral profile S_x g_x (orthonormal DST-I, FP64, the product's index reduced mod 2N);
-    // y, z: the nodal profiles; index 0 (mode 0 / boundary node) = 0
+    // x: the spectral profile S_x g_x (orthonormal DST-I) or H_x g_x (orthonormal DHT), FP64, the
+    // product's index reduced mod 2N (mod N); y, z: the nodal profiles; Dirichlet index 0 = 0
     const size_t tot = (size_t)pl->nx + pl->ny + pl->nz;
     std::vector<double> h(tot, 0.0);
     {
       const long long N = n[0];
-      const double s0 = std::sqrt(2.0 / (double)N);
-      for (long long k = 1; k < N; ++k) {
-        double acc = 0.0;
-        for (long long j = 1; j < N; ++j) acc += g[0][j - 1] * std::sin(M_PI * (double)((j * k) % (2 * N)) / (double)N);
-        h[k] = s0 * acc;
+      if (pl->periodic) {
+        const double s0 = 1.0 / std::sqrt((double)N);
+        for (long long k = 0; k < N; ++k) {
+          double acc = 0.0;
+          for (long long j = 0; j < N; ++j) {
+            const double t = 2.0 * M_PI * (double)((j * k) % N) / (double)N;
+            acc += g[0][j] * (std::cos(t) + std::sin(t));
+          }
+          h[k] = s0 * acc;
+        }
+      } else {
+        const double s0 = std::sqrt(2.0 / (double)N);
+        for (long long k = 1; k < N; ++k) {
+          double acc = 0.0;
+          for (long long j = 1; j < N; ++j) acc += g[0][j - 1] * std::sin(M_PI * (double)((j * k) % (2 * N)) / (double)N);
+          h[k] = s0 * acc;
+        }
       }
     }
     size_t off = (size_t)n[0];
     for (int d = 1; d < pl->ndim; ++d) {
-      for (int i = 1; i < n[d]; ++i) h[off + i] = g[d][i - 1];
+      for (int i = cut; i < n[d]; ++i) h[off + i] = g[d][i - cut];
       off += n[d];
     }
     if (!pl->src_tab) ETD_CUDA(cudaMalloc(&pl->src_tab, tot * pl->elem));
@@ -1312,10 +1347,14 @@ etd_status etd_monitor(etd_plan pl, const void* u, etd_monitors* out, void* stre
   MonitorGeom g;
   g.ndim = pl->ndim;
   for (int a = 0; a < 3; ++a) {
-    g.m[a] = a < pl->ndim ? (int)pl->N[a] - 1 : 1;
+    g.m[a] = a < pl->ndim ? (int)pl->N[a] - (pl->periodic ? 0 : 1) : 1;
     g.h[a] = a < pl->ndim ? pl->h[a] : 1.0;
   }
   g.D = pl->D;
+  g.periodic = pl->periodic;
+  g.flin = pl->opt.flin;
+  g.fcub = pl->opt.fcub;
+  g.flog = pl->opt.flog;
   if (pl->elem == 4)
     monitor_partial_kernel<float><<<pl->mon_blocks, 256, 0, s>>>(static_cast<const float*>(u), g, pl->mon_part, pl->mon_bad);
   else
@@ -1438,6 +1477,9 @@ etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const d
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
   const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
   if (gemm) return fail(ETD_ERR_UNSUPPORTED, "batches run the FFT routes only");
+  if (o.bc != ETD_BC_DIRICHLET) return fail(ETD_ERR_UNSUPPORTED, "batches take Dirichlet boundaries only");
+  if (!std::isfinite(o.flog)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
+  if (o.flog != 0.0) return fail(ETD_ERR_UNSUPPORTED, "batches take the polynomial reaction only (flog = 0)");
   for (int i = 0; i < count; ++i) {
     for (int a = 0; a < 2; ++a) {
       const int64_t n = N[2 * i + a];

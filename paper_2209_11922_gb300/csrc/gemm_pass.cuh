@@ -5,7 +5,9 @@
 // A field is a pitched array of R rows of K = N_a values, the contracted axis a contiguous (index 0
 // of every axis is the boundary, value 0). One pass computes C = X S_a, C[r][k] = sum_j X[r][j]
 // S_a[j][k] with S_a[j][k] = sqrt(2/N_a) sin(j k pi / N_a) (j, k < N_a; row and column 0 vanish, so
-// boundary values stay 0), and writes epi(C[r][k]) to out[k * R + r]. Writing the transpose rotates
+// boundary values stay 0), and writes epi(C[r][k]) to out[k * R + r]. Periodic plans contract with
+// the orthonormal Hartley matrix N_a^{-1/2} cas(2 pi j k / N_a) instead (every index is a node), which
+// is also symmetric and its own inverse; the pass itself does not depend on the matrix. Writing the transpose rotates
 // the axes: [z][y][x] -> [x][z][y] -> [y][x][z] -> [z][y][x] (2D: [y][x] -> [x][y] -> [y][x]), so
 // every pass contracts a contiguous axis and d passes return to the starting layout.
 //
@@ -46,7 +48,7 @@ struct GemmArgs {
   const float* zx; const float* ex; const float* cx;
   const float* zy; const float* ey; const float* cy;
   const float* zk; const float* ek; const float* ck;
-  float tau, c2, flin, fcub;
+  float tau, c2, flin, fcub, flog;   // f(u) = flin u + fcub u^3 + flog artanh u
   int* err;          // set to 1 by a CTA whose wait ran out
   int stall;         // test of the failure path: the accumulator-ready signal is withheld
 };
@@ -142,7 +144,11 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t trow, 
     if (op == GE_REACT) {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (j < nv) o0[j * R] = v[j] * (flin + fcub * v[j] * v[j]);
+        if (j < nv) {
+          float fr = v[j] * (flin + fcub * v[j] * v[j]);
+          if (g.flog != 0.f) fr += g.flog * atanhf(v[j]);
+          o0[j * R] = fr;
+        }
       continue;
     }
     // spectral combination

@@ -2,10 +2,13 @@
 //
 // M and K are the assembled Q1 matrices of eq. (4.1) (M = A_x (x) A_y [(x) A_z],
 // K = D sum_a B_a (x) A_others), applied as their 3^d-point nodal stencils with zero Dirichlet
-// values outside the interior:
+// values outside the interior (periodic: indices wrap around):
 //   A_a: (h_a/6) [1 4 1],  B_a: (1/h_a) [-1 2 -1].
-// The mass uses the column sums of A_a: (h_a/6)(4 + [i > 1] + [i < N_a - 1]).
-// energy = 1/2 U^T K U + sum_nodes prod(h) (u^2 - 1)^2 / 4.
+// The mass uses the column sums of A_a: (h_a/6)(4 + [i > 1] + [i < N_a - 1]) (periodic: h_a).
+// energy = 1/2 U^T K U + sum_nodes prod(h) G(u), G(u) = (u^2 - 1)^2 / 4 when flog = 0, else the
+// potential with G' = -f and G(0) = 0 of f = flin u + fcub u^3 + flog artanh u:
+// G(u) = -flog (u artanh u + ln(1 - u^2)/2) - flin u^2/2 - fcub u^4/4 (the Flory-Huggins energy
+// density of Example 5.3 for flin = theta_c, fcub = 0, flog = -theta).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -14,9 +17,11 @@ namespace etd {
 
 struct MonitorGeom {
   int ndim;
-  int m[3];        // dense extents N_a - 1 (m[2] = 1 in 2D)
+  int m[3];        // dense extents N_a - 1 (periodic: N_a; m[2] = 1 in 2D)
   double h[3];
   double D;
+  int periodic;    // 1: stencils wrap around
+  double flin, fcub, flog;   // reaction of the potential term (flog = 0: the double well)
 };
 
 template <class T>
@@ -47,19 +52,21 @@ __global__ void __launch_bounds__(256) monitor_partial_kernel(const T* __restric
     double w = 1.0;
     const int ii[3] = {i, j, k};
     for (int a = 0; a < g.ndim; ++a)
-      w *= g.h[a] / 6.0 * (4.0 + (ii[a] > 0 ? 1.0 : 0.0) + (ii[a] < g.m[a] - 1 ? 1.0 : 0.0));
+      w *= g.periodic ? g.h[a] : g.h[a] / 6.0 * (4.0 + (ii[a] > 0 ? 1.0 : 0.0) + (ii[a] < g.m[a] - 1 ? 1.0 : 0.0));
     s_mass += w * v;
     // (K U) at this node from the 3^d stencil
     double ku = 0.0;
     const int kz = g.ndim == 3 ? 1 : 0;
+    // periodic axes wrap (their extents are >= 4, so the three stencil nodes are distinct)
+    auto wrap = [&](int v, int n) { return g.periodic ? (v < 0 ? v + n : (v >= n ? v - n : v)) : v; };
     for (int dz = -kz; dz <= kz; ++dz) {
-      const int zz = k + dz;
+      const int zz = wrap(k + dz, g.m[2]);
       if (zz < 0 || zz >= g.m[2]) continue;
       for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = j + dy;
+        const int yy = wrap(j + dy, g.m[1]);
         if (yy < 0 || yy >= g.m[1]) continue;
         for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = i + dx;
+          const int xx = wrap(i + dx, g.m[0]);
           if (xx < 0 || xx >= g.m[0]) continue;
           const double un = (double)u[((long long)zz * g.m[1] + yy) * g.m[0] + xx];
           const int d[3] = {dx + 1, dy + 1, dz + 1};
@@ -75,7 +82,10 @@ __global__ void __launch_bounds__(256) monitor_partial_kernel(const T* __restric
       }
     }
     s_quad += 0.5 * v * ku;
-    s_pot += cell * 0.25 * (v * v - 1.0) * (v * v - 1.0);
+    if (g.flog != 0.0)
+      s_pot += cell * (-g.flog * (v * atanh(v) + 0.5 * log1p(-v * v)) - 0.5 * g.flin * v * v - 0.25 * g.fcub * v * v * v * v);
+    else
+      s_pot += cell * 0.25 * (v * v - 1.0) * (v * v - 1.0);
     s_max = fmax(s_max, fabs(v));
   }
   __shared__ double sh[4][256];

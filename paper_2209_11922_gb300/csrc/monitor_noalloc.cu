@@ -70,6 +70,10 @@ extern "C" etd_status etd_monitor_noalloc(int ndim, const int64_t* N, const doub
     }
   }
   g.D = D;
+  g.periodic = 0;   // homogeneous Dirichlet and the Allen-Cahn double well
+  g.flin = 1.0;
+  g.fcub = -1.0;
+  g.flog = 0.0;
   if (n > (long long)ETD_MONITOR_NOALLOC_MAX_UNKNOWNS)
     return noalloc_fail(ETD_ERR_INVALID_ARG,
                         "%lld unknowns exceed the maximum of %d for etd_monitor_noalloc (its fixed scratch holds "

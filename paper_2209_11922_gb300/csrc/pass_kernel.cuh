@@ -1,6 +1,11 @@
 // pass_kernel.cuh - one "axis pass" of the fast EIFE solve (Section 4): a CTA stages a tile of
-// pencils of one axis in shared memory, runs a short program of DST-I transforms with fused
-// pointwise epilogues, and writes the tile back.
+// pencils of one axis in shared memory, runs a short program of DST-I transforms (DHT on periodic
+// axes, template variant V_HART) with fused pointwise epilogues, and writes the tile back.
+//
+// Homogeneous Dirichlet: index 0 of each pitched axis is the boundary node / sine mode 0 and stays
+// zero; the dense user field holds the N_a - 1 interior nodes. Periodic (V_HART kernels; a plan's
+// axes are all periodic or all Dirichlet): every index 0..N_a-1 is a node / Hartley mode and the
+// dense field is the pitched field itself.
 //
 // Pencil pairs: along x (contiguous rows) a pair is two adjacent rows; along y or z (strided) a
 // pair is two adjacent x-columns, so each row segment of the tile is already a complex pair.
@@ -9,7 +14,7 @@
 //   ENTRY     dense u -> pitched field, DST along x                              (x)
 //   EXIT      DST along x -> dense u                                             (x)
 //   PACK/UNPACK  dense <-> pitched without transform                             (x)
-//   REACT     DST, nodal reaction f(u) = flin u + fcub u^3, DST                  (x)
+//   REACT     DST, nodal reaction f(u) = flin u + fcub u^3 [+ flog artanh u], DST (x)
 //   TRANSFORM DST                                                                (any axis)
 //   RK1       last axis: DST(U), DST(N0), U~+ = e^{-z} U~ + tau phi1(-z) N0~, DST  -> eq. (2.13)
 //   S1        last axis: DST(U), DST(N0), U2~ = e^{-c2 z} U~ + c2 tau phi1(-c2 z) N0~ (DST -> out0),
@@ -38,6 +43,11 @@ enum PassOp : int {
 
 enum EpiKind : int { EPI_PLAIN = 0, EPI_REACT = 1, EPI_RK1 = 2, EPI_S1 = 3, EPI_S2 = 4 };
 
+// f(u) = flin u + fcub u^3 + flog artanh(u); flog artanh u = (flog/2) ln((1+u)/(1-u)) is the
+// Flory-Huggins term of Example 5.3 (Section 5.2).
+__device__ __forceinline__ float artanh_(float v) { return atanhf(v); }
+__device__ __forceinline__ double artanh_(double v) { return atanh(v); }
+
 template <class T> struct PassArgs {
   int op, axis, ndim;
   int nx, ny, nz;   // pitched extents; nz = 1 in 2D. Index 0 of each axis is the boundary / mode 0.
@@ -55,12 +65,12 @@ template <class T> struct PassArgs {
   const T* zeta[3]; // per paper axis: tau D mu_a
   const T* ex[3];   // exp(-tau D mu_a)
   const T* ec[3];   // exp(-c2 tau D mu_a)
-  T sc, tau, c2, flin, fcub;
+  T sc, tau, c2, flin, fcub, flog;
   // Separable time-dependent source of the reaction (REACT passes; src_gx == NULL: none). The pass
   // stores S_x f(u), so it adds src_amp exp(-src_rate t) (S_x g_x)[k] g_y[y] g_z[z] at node row
   // (y, z) and x mode k, t = t0 + (steps + src_c) tau.
-  const T* src_gx;                       // [nx] spectral x profile S_x g_x (mode 0 = 0)
-  const T* src_gy;                       // [ny] nodal y profile (boundary 0)
+  const T* src_gx;                       // [nx] spectral x profile S_x g_x (Dirichlet: mode 0 = 0)
+  const T* src_gy;                       // [ny] nodal y profile (Dirichlet: boundary 0)
   const T* src_gz;                       // [nz] nodal z profile (3D; NULL in 2D)
   const double* src_t0;                  // start time of the run
   const unsigned long long* step_ctr;    // time steps completed in the run
@@ -98,9 +108,10 @@ template <class T> __device__ __forceinline__ void count_step(const PassArgs<T>&
   }
 }
 
-template <class T, int N, bool ODD>
+template <class T, int N, int VAR>
 __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) {
-  using L = PairLayout<T, N, ODD>;
+  using L = PairLayout<T, N, VAR>;
+  constexpr bool PER = L::HART;   // periodic: no boundary planes, rows or slots
   using C = Cx<T>;
   using VT = typename V2<T>::type;
   constexpr int TPP = L::TPP;
@@ -138,14 +149,14 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     if (A.axis == 1) {
       stride = A.nx;
       base = x0 + (long long)o * A.nx * A.ny;
-      if (A.ndim == 3 && o == 0) {         // z = 0 plane: boundary, stays zero
+      if (!PER && A.ndim == 3 && o == 0) {   // z = 0 plane: boundary, stays zero
         count_step(A);
         return;
       }
     } else {
       stride = A.nx * A.ny;
       base = x0 + (long long)o * A.nx;
-      if (o == 0) {                        // y = 0 row: boundary, stays zero
+      if (!PER && o == 0) {                  // y = 0 row: boundary, stays zero
         count_step(A);
         return;
       }
@@ -236,8 +247,10 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       }
     }
   };
-  // dense user layout: rows of nx-1 interior values, only rows with y >= 1 (and z >= 1 in 3D)
+  // dense user layout: rows of nx-1 interior values, only rows with y >= 1 (and z >= 1 in 3D);
+  // periodic: the pitched layout itself
   auto dense_row = [&](int r) -> long long {
+    if constexpr (PER) return (long long)r * A.nx;
     const int y = r % A.ny, z = r / A.ny;
     if (y == 0 || (A.ndim == 3 && z == 0)) return -1;
     const long long dr = (A.ndim == 3 ? (long long)(z - 1) * (A.ny - 1) : 0LL) + (y - 1);
@@ -254,18 +267,20 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   }
   auto load_dense = [&](const T* __restrict__ src, C* buf) {
     C* bpp = buf + p * LP;
+    constexpr int X0 = PER ? 0 : 1;   // dense column of pitched index x is x - X0
     for (int x = l; x < N; x += TPP) {
-      const T a = (x > 0 && dra >= 0) ? src[dra + x - 1] : T(0);
-      const T b = (x > 0 && drb >= 0) ? src[drb + x - 1] : T(0);
+      const T a = (x >= X0 && dra >= 0) ? src[dra + x - X0] : T(0);
+      const T b = (x >= X0 && drb >= 0) ? src[drb + x - X0] : T(0);
       bpp[L::at(x)] = C{a, b};
     }
   };
   auto store_dense = [&](const C* buf, T* __restrict__ dst) {
     const C* bpp = buf + p * LP;
-    for (int x = l + (l == 0 ? TPP : 0); x < N; x += TPP) {
+    constexpr int X0 = PER ? 0 : 1;
+    for (int x = l + (l < X0 ? TPP : 0); x < N; x += TPP) {
       const C c = bpp[L::at(x)];
-      if (dra >= 0) dst[dra + x - 1] = c.x;
-      if (drb >= 0) dst[drb + x - 1] = c.y;
+      if (dra >= 0) dst[dra + x - X0] = c.x;
+      if (drb >= 0) dst[drb + x - X0] = c.y;
     }
   };
 
@@ -336,10 +351,9 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   C* const b0p = b0 + p * LP;
   C* const b1p = b1 + p * LP;
   C* const scrp = scr + p * (TPP > 32 ? TPP / 32 : 1);
-  const T tau = A.tau, c2 = A.c2, flin = A.flin, fcub = A.fcub, inv_c2 = T(1) / A.c2;
+  const T tau = A.tau, c2 = A.c2, inv_c2 = T(1) / A.c2;
 
   auto epilogue = [&](int kind, int j, C w) -> C {
-    if (kind == EPI_REACT) return C{w.x * (flin + fcub * w.x * w.x), w.y * (flin + fcub * w.y * w.y)};
     const T zjj = zj[j], ejj = ej[j];
     T out[2];
     const T wv[2] = {w.x, w.y};
@@ -420,19 +434,31 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     if (op == OP_RK1 || op == OP_S1) {
       C* const bps[2] = {b0p, b1p};
       C* const scrs[2] = {scrp, scrp};   // unused by the odd-extension variant
-      dst_pairs<T, N, ODD, 2>(bps, tw, sn, l, scrs, A.sc);
-      epilogue_pair<T, N, ODD>(b1p, l, [&](int j, C w) -> C { return epilogue(epi[1], j, w); });
+      dst_pairs<T, N, VAR, 2>(bps, tw, sn, l, scrs, A.sc);
+      epilogue_pair<T, N, VAR>(b1p, l, [&](int j, C w) -> C { return epilogue(epi[1], j, w); });
       if (op == OP_S1) store_tile(b1, A.out1);
       s0 = 2;
     }
   }
+  // A logarithmic reaction term (flog != 0; periodic kernels only, the Flory-Huggins reaction of
+  // Example 5.3) takes an unfused pointwise pass over the nodal values before the second transform
+  // of REACT; the Dirichlet kernels are compiled without it.
+  const bool logr = PER && op == OP_REACT && A.flog != T(0);
 #pragma unroll 1
   for (int s = s0; s < nd; ++s) {
     const int kind = epi[s];
     C* bp = bsel[s] ? b1p : b0p;
-    const React<T> rx{op == OP_REACT && s == 1, flin, fcub};
-    dst_pair<T, N, ODD>(bp, tw, sn, l, scrp, A.sc, rx);
-    if (kind != EPI_PLAIN) epilogue_pair<T, N, ODD>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
+    if constexpr (PER) {
+      if (logr && s == 1) {
+        const T fl = A.flin, fc = A.fcub, fg = A.flog;
+        epilogue_pair<T, N, VAR>(bp, l, [&](int, C w) -> C {
+          return C{w.x * (fl + fc * w.x * w.x) + fg * artanh_(w.x), w.y * (fl + fc * w.y * w.y) + fg * artanh_(w.y)};
+        });
+      }
+    }
+    const React<T> rx{op == OP_REACT && s == 1 && !logr, A.flin, A.fcub};
+    dst_pair<T, N, VAR>(bp, tw, sn, l, scrp, A.sc, rx);
+    if (kind != EPI_PLAIN) epilogue_pair<T, N, VAR>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
 
@@ -461,15 +487,15 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
 }
 
 // One plan: the launch covers the tiles of one field.
-template <class T, int N, bool ODD>
+template <class T, int N, int VAR>
 __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(const PassArgs<T> A) {
-  pass_body<T, N, ODD>(A, (int)blockIdx.x);
+  pass_body<T, N, VAR>(A, (int)blockIdx.x);
 }
 
 // Batches: one launch covers the tiles of many independent problems whose transformed axis has
 // length N. CTA b works on tile map[b].y of the problem described by descs[map[b].x]; entry and exit
 // passes take the caller's field pointer from user[descs[.].user_slot].
-template <class T, int N, bool ODD>
+template <class T, int N, int VAR>
 __global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
     pass_kernel_batched(const PassArgs<T>* __restrict__ descs, const int2* __restrict__ map, T* const* __restrict__ user) {
   const int2 m = map[blockIdx.x];
@@ -478,7 +504,7 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
     if (A.op == OP_ENTRY || A.op == OP_PACK) A.in0 = user[A.user_slot];
     else A.out0 = user[A.user_slot];
   }
-  pass_body<T, N, ODD>(A, m.y);
+  pass_body<T, N, VAR>(A, m.y);
 }
 
 // Host-side description of one instantiation.
@@ -489,8 +515,8 @@ struct KernelInfo {
   int tpp;
   int lp;
   int elem;   // sizeof(T)
-  int fft_len;  // M: 2N (odd extension) or N (recurrence)
-  int odd;      // 1: odd-extension variant, 0: recurrence variant
+  int fft_len;  // M: 2N (odd extension) or N (recurrence, Hartley)
+  int odd;      // transform variant: V_ODD odd extension, V_REC recurrence, V_HART Hartley
   int padg;     // one padding slot every padg positions
   int twn;      // twiddle table entries
   int radix[4]; // Stockham radices (0-terminated)
@@ -502,12 +528,12 @@ template <int... Rs> void radix_list(int* out, Radices<Rs...>) {
   for (int i = 0; i < 4; ++i) out[i] = i < (int)sizeof...(Rs) ? r[i] : 0;
 }
 
-template <class T, int N, bool ODD> KernelInfo kernel_info() {
-  using L = PairLayout<T, N, ODD>;
-  KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, ODD>),
-               reinterpret_cast<const void*>(&pass_kernel_batched<T, N, ODD>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
-               ODD ? 1 : 0, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
-  radix_list(k.radix, typename FftPlan<T, N, ODD>::R{});
+template <class T, int N, int VAR> KernelInfo kernel_info() {
+  using L = PairLayout<T, N, VAR>;
+  KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, VAR>),
+               reinterpret_cast<const void*>(&pass_kernel_batched<T, N, VAR>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
+               VAR, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
+  radix_list(k.radix, typename L::Plan::R{});
   return k;
 }
 

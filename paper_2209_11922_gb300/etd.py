@@ -13,6 +13,7 @@ import numpy as np
 from . import _native as nat
 
 _DT = {"f64": nat.ETD_F64, "f32": nat.ETD_F32}
+_BC = {"dirichlet": nat.ETD_BC_DIRICHLET, "periodic": nat.ETD_BC_PERIODIC}
 _ROUTE = {"auto": nat.ETD_ROUTE_AUTO, "fft": nat.ETD_ROUTE_FFT, "fft_half": nat.ETD_ROUTE_FFT_HALF,
           "gemm_tf32": nat.ETD_ROUTE_GEMM_TF32, "gemm_bf16x3": nat.ETD_ROUTE_GEMM_BF16X3}
 
@@ -33,12 +34,15 @@ class Plan:
     """EIFE1/EIFE2 plan for u_t = D Lap u + flin u + fcub u^3 on a rectangle (2D or 3D).
 
     N: intervals per axis (N_x first); h: mesh sizes (default 1/N, the unit square/cube).
-    Fields are torch tensors of shape (N_z-1, N_y-1, N_x-1) or (N_y-1, N_x-1), x fastest.
+    Fields are torch tensors of shape (N_z-1, N_y-1, N_x-1) or (N_y-1, N_x-1), x fastest; with
+    bc="periodic" every node is an unknown, (N_z, N_y, N_x) or (N_y, N_x).
+    The reaction is f(u) = flin u + fcub u^3 + flog artanh(u) (Flory-Huggins, Example 5.3:
+    flin = theta_c, fcub = 0, flog = -theta).
     """
 
     def __init__(self, N: Sequence[int], D: float, tau: float, scheme: int = 2, dtype: str = "f64",
                  h: Optional[Sequence[float]] = None, c2: float = 0.5, flin: float = 1.0, fcub: float = -1.0,
-                 route: str = "auto", debug: int = 0):
+                 route: str = "auto", debug: int = 0, bc: str = "dirichlet", flog: float = 0.0):
         L = nat.lib()
         self.N = tuple(int(n) for n in N)
         self.ndim = len(self.N)
@@ -50,8 +54,12 @@ class Plan:
         L.etd_options_default(ctypes.byref(opt))
         opt.dtype = _DT[dtype]
         opt.route = _ROUTE[route]
-        opt.c2, opt.flin, opt.fcub = float(c2), float(flin), float(fcub)
+        opt.c2, opt.flin, opt.fcub, opt.flog = float(c2), float(flin), float(fcub), float(flog)
         opt.debug = int(debug)
+        if bc not in _BC:
+            raise ValueError("bc must be 'dirichlet' or 'periodic'")
+        opt.bc = _BC[bc]
+        self.bc = bc
         Na = (ctypes.c_int64 * 3)(*(list(self.N) + [1] * (3 - self.ndim)))
         ha = (ctypes.c_double * 3)(*(list(self.h) + [1.0] * (3 - self.ndim)))
         handle = ctypes.c_void_p()
@@ -62,7 +70,8 @@ class Plan:
     # ------------------------------------------------------------------ helpers
     @property
     def shape(self) -> tuple:
-        return tuple(n - 1 for n in reversed(self.N))
+        cut = 0 if self.bc == "periodic" else 1
+        return tuple(n - cut for n in reversed(self.N))
 
     @property
     def torch_dtype(self):
@@ -89,7 +98,8 @@ class Plan:
 
     def set_source(self, amp: float, rate: float, *profiles):
         """Separable time-dependent source amp exp(-rate t) g_x[i] g_y[j] (g_z[k]) added to the reaction;
-        one profile of N_a - 1 interior values per axis (x first); no profiles removes it."""
+        one profile of N_a - 1 interior values per axis (periodic: N_a nodal values), x first; no
+        profiles removes it."""
         L = nat.lib()
         if not profiles or all(g is None for g in profiles):
             nat.check(L.etd_set_source(self._h, 0.0, 0.0, None, None, None), "etd_set_source")
@@ -98,8 +108,9 @@ class Plan:
             raise ValueError("one profile per axis")
         gs = [np.ascontiguousarray(g, dtype=np.float64) for g in profiles]
         for a, g in enumerate(gs):
-            if g.shape != (self.N[a] - 1,):
-                raise ValueError(f"profile {a} must hold the N_{a} - 1 = {self.N[a] - 1} interior values")
+            n = self.shape[self.ndim - 1 - a]
+            if g.shape != (n,):
+                raise ValueError(f"profile {a} must hold the {n} nodal values of axis {a}")
         P = ctypes.POINTER(ctypes.c_double)
         ptrs = [g.ctypes.data_as(P) for g in gs] + [None] * (3 - self.ndim)
         nat.check(L.etd_set_source(self._h, float(amp), float(rate), *ptrs), "etd_set_source")

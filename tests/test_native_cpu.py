@@ -70,6 +70,7 @@ def test_defaults_and_names(L):
     opt = nat.EtdOptions()
     assert L.etd_options_default(ctypes.byref(opt)) == nat.ETD_OK
     assert (opt.dtype, opt.c2, opt.flin, opt.fcub) == (nat.ETD_F64, 0.5, 1.0, -1.0)
+    assert (opt.bc, opt.flog, opt.debug) == (nat.ETD_BC_DIRICHLET, 0.0, 0)
     assert L.etd_status_string(nat.ETD_ERR_NONFINITE) == b"non-finite values"
     assert [L.etd_pass_kind_name(k) for k in range(nat.ETD_NUM_PASS_KINDS)][1] == b"x_react"
     assert L.etd_pass_kind_name(99) is None
@@ -152,3 +153,32 @@ def test_sno_parameter_layout_round_trips():
     back = sno.unflatten(flat, 3, 2, 2)
     for k in sno.PARAM_NAMES:
         assert np.allclose(back[k], np.asarray(P[k], dtype=np.float32)), k
+
+
+def test_periodic_and_log_reaction_arguments_rejected_on_the_host(L):
+    opt = _opts(L, nat.ETD_F32)
+    opt.bc = 5
+    st, p = _create(L, 2, (64, 64, 1), (1 / 64, 1 / 64, 1.0), opt=ctypes.byref(opt))
+    assert st == nat.ETD_ERR_INVALID_ARG and not p.value
+    opt = _opts(L, nat.ETD_F32)
+    opt.flog = float("nan")
+    st, p = _create(L, 2, (64, 64, 1), (1 / 64, 1 / 64, 1.0), opt=ctypes.byref(opt))
+    assert st == nat.ETD_ERR_INVALID_ARG and not p.value
+    for route in (nat.ETD_ROUTE_GEMM_TF32, nat.ETD_ROUTE_GEMM_BF16X3):
+        opt = _opts(L, nat.ETD_F32, route)
+        opt.bc = nat.ETD_BC_PERIODIC
+        st, p = _create(L, 2, (64, 48, 1), (1 / 64, 1 / 48, 1.0), opt=ctypes.byref(opt))
+        assert st == nat.ETD_ERR_UNSUPPORTED and not p.value     # multiples of 32 on these routes too
+    opt = _opts(L, nat.ETD_F32)
+    opt.flog = -0.8                     # the artanh term: periodic plans and GEMM routes only
+    st, p = _create(L, 2, (64, 64, 1), (1 / 64, 1 / 64, 1.0), opt=ctypes.byref(opt))
+    assert st == nat.ETD_ERR_UNSUPPORTED and not p.value
+    opt = _opts(L, nat.ETD_F32)
+    opt.bc = nat.ETD_BC_PERIODIC
+    st, p = _create(L, 2, (64, 80, 1), (1 / 64, 1 / 80, 1.0), opt=ctypes.byref(opt))
+    assert st == nat.ETD_ERR_UNSUPPORTED and not p.value     # no kernel for 80
+    b = ctypes.c_void_p()
+    N = (ctypes.c_int64 * 2)(64, 64)
+    h = (ctypes.c_double * 2)(1 / 64, 1 / 64)
+    D = (ctypes.c_double * 1)(1e-3)
+    assert L.etd_batch_create(ctypes.byref(b), 1, N, h, D, 0.01, 2, ctypes.byref(opt)) == nat.ETD_ERR_UNSUPPORTED

@@ -255,3 +255,17 @@ def test_example53_keeps_the_max_bound_and_decays_the_energy():
         assert m["energy"] <= E + 1e-14
         E = m["energy"]
     assert m["maxabs"] > 0.9 * g   # the field has separated into the two phases
+
+
+# ---------------------------------------------------------------- the Hartley transform (kernel-level oracle)
+@pytest.mark.parametrize("N", [4, 6, 16, 48])
+def test_hartley_matrix_is_the_real_form_of_the_dft(N):
+    from oracle import transforms
+    H = transforms.hartley_matrix(N)
+    F = np.fft.fft(np.eye(N), axis=0)          # F_jk = exp(-2 pi i j k / N)
+    np.testing.assert_allclose(H, (F.real - F.imag) / np.sqrt(N), atol=1e-14)
+    np.testing.assert_allclose(H @ H, np.eye(N), atol=1e-13)
+    A, B = fem.assemble_1d(N, 1.0 / N, "periodic")
+    th = 2 * np.pi * np.arange(N) / N
+    np.testing.assert_allclose(H @ A @ H, np.diag((2 + np.cos(th)) / (3 * N)), atol=1e-14)
+    np.testing.assert_allclose(H @ B @ H, np.diag(2 * N * (1 - np.cos(th))), atol=1e-10)
