@@ -18,6 +18,7 @@ Everything is FP64 NumPy/SciPy, written for readability, not speed:
                eqs. (4.2)-(4.4), with dense per-axis products (tensor mode products of Section 4).
 * ``monitors`` mass 1^T M U, the discrete energy, max|u|.
 * ``transforms`` the orthonormal DST-I of one axis from its definition (kernel-level parity).
+* ``boundary`` nonhomogeneous Dirichlet data as a time-dependent part of f (Section 4).
 * ``sno``      the spectral neural operator used as the learned coarse propagator (forward pass,
                its chain-rule gradient, Adam) and the Parareal iteration.
 
@@ -38,4 +39,4 @@ Readings of the paper taken here:
 Parity status of each function is stated in its docstring; functions without an independent pin
 say "parity unpinned".
 """
-from . import fem, spectral, phi, etd, monitors, transforms, sno  # noqa: F401
+from . import fem, spectral, phi, etd, monitors, transforms, sno, boundary  # noqa: F401

@@ -69,6 +69,23 @@ def assemble_1d(N: int, h: float, bc: str = "dirichlet") -> tuple[np.ndarray, np
     return Af[1:N, 1:N].copy(), Bf[1:N, 1:N].copy()
 
 
+def assemble_1d_all_nodes(N: int, h: float) -> tuple[np.ndarray, np.ndarray]:
+    """The 1D mass and stiffness over N elements on all N+1 nodes (boundary rows included), as
+    needed for nonhomogeneous Dirichlet data: the interior rows couple the interior unknowns to the
+    prescribed boundary values through the columns of nodes 0 and N."""
+    if N < 2:
+        raise ValueError("need at least two intervals")
+    A = np.zeros((N + 1, N + 1))
+    B = np.zeros((N + 1, N + 1))
+    me, ke = element_mass_1d(h), element_stiffness_1d(h)
+    for e in range(N):
+        for a in range(2):
+            for b in range(2):
+                A[e + a, e + b] += me[a, b]
+                B[e + a, e + b] += ke[a, b]
+    return A, B
+
+
 def element_matrices_nd(h: tuple, D: float) -> tuple[np.ndarray, np.ndarray]:
     """Q1 element mass and stiffness in d dimensions (local nodes ordered x fastest).
 
@@ -91,6 +108,33 @@ def element_matrices_nd(h: tuple, D: float) -> tuple[np.ndarray, np.ndarray]:
                 k1[a][ip[a], iq[a]] * np.prod([m1[b][ip[b], iq[b]] for b in range(d) if b != a])
                 for a in range(d))
     return Me, Ke
+
+
+def assemble_global_all_nodes(N: tuple, h: tuple, D: float) -> tuple[sp.csr_matrix, sp.csr_matrix, np.ndarray]:
+    """Global M and K over all (N_x+1)(N_y+1)[(N_z+1)] nodes (x fastest) and the indices of the
+    interior nodes among them, from the element matrices (no Kronecker form)."""
+    d = len(N)
+    Me, Ke = element_matrices_nd(h, D)
+    full = [n + 1 for n in N]
+    strides = [int(np.prod(full[:a])) for a in range(d)]
+    rows, cols, mv, kv = [], [], [], []
+    locs = [tuple((n >> a) & 1 for a in range(d)) for n in range(2 ** d)]
+    for e in itertools.product(*[range(n) for n in reversed(N)]):
+        e = tuple(reversed(e))
+        nodes = [sum((e[a] + lp[a]) * strides[a] for a in range(d)) for lp in locs]
+        for p in range(len(nodes)):
+            for q in range(len(nodes)):
+                rows.append(nodes[p])
+                cols.append(nodes[q])
+                mv.append(Me[p, q])
+                kv.append(Ke[p, q])
+    ntot = int(np.prod(full))
+    interior = []
+    for idx in itertools.product(*[range(1, n) for n in reversed(N)]):
+        idx = tuple(reversed(idx))
+        interior.append(sum(idx[a] * strides[a] for a in range(d)))
+    return (sp.coo_matrix((mv, (rows, cols)), shape=(ntot, ntot)).tocsr(),
+            sp.coo_matrix((kv, (rows, cols)), shape=(ntot, ntot)).tocsr(), np.array(interior))
 
 
 def assemble_global(N: tuple, h: tuple, D: float, bc: str = "dirichlet") -> tuple[sp.csr_matrix, sp.csr_matrix]:

@@ -97,3 +97,36 @@ def test_flory_huggins_log_sign_error_is_caught(monkeypatch):
         lambda t, u: 0.5 * th * np.log((1.0 + u) / (1.0 - u)) + thc * u))
     with pytest.raises(AssertionError):
         periodic_pins.test_periodic_eigen_path_matches_dense_expm((4, 5), (0.25, 0.2), 1, "flory_huggins")
+
+
+# ---------------------------------------------------------------- nonhomogeneous Dirichlet data
+import test_oracle_boundary as boundary_pins
+from oracle import boundary as obnd
+
+
+def _planted_source(monkeypatch, drop_gdot=False, flip_k=False):
+    orig = obnd.boundary_source
+
+    def bad(N, h, D, f, data):
+        def data2(t):
+            g, gd = data(t)
+            return g, (0 * gd if drop_gdot else gd)
+        src = orig(N, h, -D if flip_k else D, f, data2)   # flipping D flips the K_IB g term only
+        return src
+    monkeypatch.setattr(obnd, "boundary_source", bad)
+
+
+def test_boundary_pins_pass_unmutated():
+    boundary_pins.test_example52_converges_to_the_semidiscrete_solution(2, 2.0)
+
+
+def test_dropped_boundary_time_derivative_is_caught(monkeypatch):
+    _planted_source(monkeypatch, drop_gdot=True)
+    with pytest.raises(AssertionError):
+        boundary_pins.test_example52_converges_to_the_semidiscrete_solution(2, 2.0)
+
+
+def test_boundary_stiffness_sign_error_is_caught(monkeypatch):
+    _planted_source(monkeypatch, flip_k=True)
+    with pytest.raises(AssertionError):
+        boundary_pins.test_linear_field_is_a_discrete_steady_state((6, 5), (1 / 6, 0.2), 2)
