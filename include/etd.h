@@ -150,6 +150,31 @@ etd_status etd_set_source(etd_plan plan, double amp, double rate, const double* 
  * t). etd_run is etd_run_from with t0 = 0. */
 etd_status etd_run_from(etd_plan plan, void* u, int64_t nsteps, double t0, void* stream);
 
+/* Nonhomogeneous Dirichlet data (Section 4: the given boundary values of the solution enter the
+ * scheme as part of f; Example 5.2 of Section 5). The Galerkin system on all nodes with the boundary
+ * nodal values g(t) prescribed has the interior rows
+ *   M_II U' + K_II U = M_II f(U) + b(t),  b(t) = M_IB (f(g) - g'(t)) - K_IB g(t)
+ * (the reaction taken on nodal values of every node), so each stage adds M_II^{-1} b(t) to the nodal
+ * reaction: b is assembled on the GPU from the boundary values by the Q1 stencils, transformed along
+ * every axis, scaled by the inverse mass eigenvalues and transformed back along the last axis.
+ * `fn` supplies the data: fn(t, g, gdot, ctx) writes the boundary values and their time derivatives
+ * at time t into the HOST arrays g[count] and gdot[count] (count from etd_boundary_count) and returns
+ * 0 (nonzero aborts the run with ETD_ERR_INVALID_ARG). Layout, faces in the order x = 0, x = L_x,
+ * y = 0, y = L_y (, z = 0, z = L_z), each over all its nodes including edges and corners, x fastest
+ * within a face: 3D x-faces [N_z+1][N_y+1], y-faces [N_z+1][N_x+1], z-faces [N_y+1][N_x+1]; 2D
+ * x-faces [N_y+1], y-faces [N_x+1]. A node on several faces takes its value from the first of them
+ * in that order. The run calls fn at every stage time (t_n, and t_n + c2 tau for EIFE2), copies the
+ * arrays to the device and synchronises `stream` once per time step (no CUDA graph), so such runs
+ * are for accuracy, not speed. fn NULL removes the data (homogeneous Dirichlet again).
+ * Errors: ETD_ERR_INVALID_ARG (periodic plan), ETD_ERR_UNSUPPORTED (GEMM routes), ETD_ERR_OOM. */
+typedef int (*etd_boundary_fn)(double t, double* g, double* gdot, void* ctx);
+etd_status etd_set_boundary(etd_plan plan, etd_boundary_fn fn, void* ctx);
+
+/* Number of boundary nodal values per array of the layout above: 2D 2(N_y+1) + 2(N_x+1); 3D
+ * 2(N_z+1)(N_y+1) + 2(N_z+1)(N_x+1) + 2(N_y+1)(N_x+1). Errors: ETD_ERR_INVALID_ARG (NULL argument or a
+ * periodic plan). */
+etd_status etd_boundary_count(etd_plan plan, int64_t* count);
+
 /* Same as etd_run, but u_host is HOST memory (pinned or pageable) of the field's size: the call
  * copies it to a plan-owned device buffer, runs, copies the result back and synchronises the
  * stream before returning. */
@@ -182,8 +207,9 @@ etd_status etd_monitor(etd_plan plan, const void* u, etd_monitors* out, void* st
 /* Kernel-level timing of one etd_run: records CUDA events around every kernel launch, runs
  * `nsteps` steps on `stream`, synchronises, and writes per pass kind the summed duration in
  * milliseconds and the launch count (arrays of length ETD_NUM_PASS_KINDS). Not for production
- * use: the events add launch overhead. */
-#define ETD_NUM_PASS_KINDS 8
+ * use: the events add launch overhead. Plans with nonhomogeneous Dirichlet data return
+ * ETD_ERR_UNSUPPORTED. */
+#define ETD_NUM_PASS_KINDS 9
 etd_status etd_run_profiled(etd_plan plan, void* u, int64_t nsteps, void* stream,
                             double* ms_per_kind, int64_t* launches_per_kind);
 

@@ -22,7 +22,7 @@ ETD_DEBUG_STALL_FIRST_GEMM_PASS = 0x5A11
 ETD_F64, ETD_F32 = 0, 1
 ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3 = 0, 1, 2, 3, 4
 ETD_BC_DIRICHLET, ETD_BC_PERIODIC = 0, 1
-ETD_NUM_PASS_KINDS = 8
+ETD_NUM_PASS_KINDS = 9
 
 
 class EtdPararealStats(ctypes.Structure):
@@ -43,6 +43,9 @@ class EtdPlanInfo(ctypes.Structure):
                 ("kernels_per_step", c_int), ("bytes_per_step", c_double), ("dtype", c_int), ("scheme", c_int)]
 
 
+# int (*etd_boundary_fn)(double t, double* g, double* gdot, void* ctx)
+BOUNDARY_FN = ctypes.CFUNCTYPE(c_int, c_double, ctypes.POINTER(c_double), ctypes.POINTER(c_double), c_void_p)
+
 _SIGS = {
     "etd_options_default": (c_int, [ctypes.POINTER(EtdOptions)]),
     "etd_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int64),
@@ -52,6 +55,8 @@ _SIGS = {
     "etd_run_from": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_void_p]),
     "etd_set_source": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                ctypes.POINTER(c_double)]),
+    "etd_set_boundary": (c_int, [c_void_p, BOUNDARY_FN, c_void_p]),
+    "etd_boundary_count": (c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "etd_run_host": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "etd_apply_dst": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "etd_monitor": (c_int, [c_void_p, c_void_p, ctypes.POINTER(EtdMonitors), c_void_p]),

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "../../include/etd.h"
+#include "boundary.cuh"
 #include "gemm_pass.cuh"
 #include "monitor.cuh"
 #include "pass_kernel.cuh"
@@ -72,9 +73,10 @@ etd_status fail(etd_status s, const char* fmt, ...) {
   } while (0)
 
 enum PassKind { PK_ENTRY_EXIT = 0, PK_REACT = 1, PK_TRANSFORM = 2, PK_S1 = 3, PK_S2 = 4, PK_RK1 = 5,
-                PK_PACK = 6, PK_MONITOR = 7 };
+                PK_PACK = 6, PK_MONITOR = 7, PK_BOUNDARY = 8 };
 const char* kPassKindNames[ETD_NUM_PASS_KINDS] = {"entry_exit", "x_react", "transform", "stage1_etdrk2",
-                                                   "stage2_etdrk2", "stage_etdrk1", "pack", "monitor"};
+                                                   "stage2_etdrk2", "stage_etdrk1", "pack", "monitor",
+                                                   "boundary"};
 
 struct Launch {
   const void* fn;
@@ -143,6 +145,15 @@ struct etd_plan_s {
   void* gtab = nullptr;       // sine (periodic: Hartley) matrices S_a (fp32 TF32-rounded, or bf16 hi and lo)
   const void* gS[3][2] = {};  // per axis: S (TF32) or S_hi, S_lo (BF16x3)
   int* dev_err = nullptr;     // set by a tensor-core pass whose wait ran out
+  // nonhomogeneous Dirichlet data (etd_set_boundary)
+  bool bnd_on = false;
+  etd_boundary_fn bnd_fn = nullptr;
+  void* bnd_ctx = nullptr;
+  int64_t bnd_count = 0;
+  double* bnd_host = nullptr;  // pinned: per stage, values [count] then time derivatives [count]
+  double* bnd_dev = nullptr;   // device copy of bnd_host
+  void* bnd_field = nullptr;   // pitched B field of the plan's dtype
+  double* bnd_ia = nullptr;    // 1 / lambda^A per axis: [nx], [ny], [nz]
 };
 
 namespace {
@@ -279,6 +290,7 @@ void apply_source(etd_plan_s* pl) {
   const T* tab = static_cast<const T*>(pl->src_tab);
   int nreact = 0;
   for (Launch& L : pl->step) {
+    if (L.kind == PK_BOUNDARY) continue;   // boundary-data launches (their transforms are not REACT)
     PassArgs<T>* a = reinterpret_cast<PassArgs<T>*>(L.args);
     if (a->op != OP_REACT) continue;
     a->src_gx = tab;
@@ -298,6 +310,69 @@ __global__ void source_clock_kernel(unsigned long long* steps, double* t0p, doub
   *t0p = t0;
 }
 
+// A launch of one of the boundary-data kernels (boundary.cuh) on the plan's B field.
+template <class T>
+Launch bnd_launch(const etd_plan_s* pl, const void* fn, const BndArgs<T>& a, double fields_rw) {
+  static_assert(sizeof(BndArgs<T>) <= sizeof(Launch::args), "launch argument buffer too small");
+  Launch L;
+  L.fn = fn;
+  const long long blocks = (a.n + 255) / 256;
+  L.grid = dim3((unsigned)(blocks < 4LL * pl->num_sms ? blocks : 4LL * pl->num_sms));
+  L.block = dim3(256);
+  L.smem = 0;
+  L.kind = PK_BOUNDARY;
+  memcpy(L.args, &a, sizeof(a));
+  L.args_size = sizeof(a);
+  L.alg_bytes = fields_rw * (double)pl->nfield * sizeof(T);
+  return L;
+}
+
+// Appends the launches that add M_II^{-1} b(t_stage) to the reaction field `target` (pitched, spectral
+// along every axis but the last): BUILD, DST along every axis, SCALE, DST along the last axis, ADD.
+template <class T>
+etd_status append_boundary(etd_plan_s* pl, int stage, void* target, std::vector<Launch>& out) {
+  BndArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.ndim = pl->ndim;
+  a.nx = pl->nx;
+  a.ny = pl->ny;
+  a.nz = pl->nz;
+  a.n = (long long)pl->nfield;
+  T* B = static_cast<T*>(pl->bnd_field);
+  a.out = B;
+  a.g = pl->bnd_dev + (size_t)stage * 2 * pl->bnd_count;
+  a.count = pl->bnd_count;
+  const long long Nx = pl->nx, Ny = pl->ny, Nz = pl->nz;
+  if (pl->ndim == 3) {
+    const long long fx = (Nz + 1) * (Ny + 1), fy = (Nz + 1) * (Nx + 1), fz = (Ny + 1) * (Nx + 1);
+    const long long sz[6] = {fx, fx, fy, fy, fz, fz};
+    for (int f = 1; f < 6; ++f) a.off[f] = a.off[f - 1] + sz[f - 1];
+  } else {
+    const long long sz[4] = {Ny + 1, Ny + 1, Nx + 1, Nx + 1};
+    for (int f = 1; f < 4; ++f) a.off[f] = a.off[f - 1] + sz[f - 1];
+  }
+  for (int d = 0; d < 3; ++d) a.h[d] = d < pl->ndim ? pl->h[d] : 1.0;
+  a.D = pl->D;
+  a.flin = pl->opt.flin;
+  a.fcub = pl->opt.fcub;
+  a.ia[0] = pl->bnd_ia;
+  a.ia[1] = pl->bnd_ia + Nx;
+  a.ia[2] = pl->bnd_ia + Nx + Ny;
+  out.push_back(bnd_launch<T>(pl, reinterpret_cast<const void*>(&bnd_build_kernel<T>), a, 1));
+  Launch L;
+  etd_status st;
+  for (int ax = 0; ax <= pl->ndim; ++ax) {   // every axis, then the last axis again after SCALE
+    const int axis = ax < pl->ndim ? ax : pl->ndim - 1;
+    if (ax == pl->ndim) out.push_back(bnd_launch<T>(pl, reinterpret_cast<const void*>(&bnd_scale_kernel<T>), a, 2));
+    if ((st = make_launch<T>(pl, OP_TRANSFORM, axis, B, nullptr, B, nullptr, PK_BOUNDARY, 2, L)) != ETD_OK) return st;
+    out.push_back(L);
+  }
+  a.out = static_cast<T*>(target);
+  a.in = B;
+  out.push_back(bnd_launch<T>(pl, reinterpret_cast<const void*>(&bnd_add_kernel<T>), a, 3));
+  return ETD_OK;
+}
+
 template <class T>
 etd_status build_step(etd_plan_s* pl) {
   void** F = pl->F;
@@ -311,30 +386,41 @@ etd_status build_step(etd_plan_s* pl) {
     if (st != ETD_OK) return st;                                                               \
     pl->step.push_back(L);                                                                     \
   } while (0)
+  // nonhomogeneous Dirichlet data: the stage's reaction field receives M_II^{-1} b(t_stage)
+#define BND(stage, field)                                                                      \
+  do {                                                                                         \
+    if (pl->bnd_on && (st = append_boundary<T>(pl, stage, field, pl->step)) != ETD_OK) return st; \
+  } while (0)
   if (pl->ndim == 2) {
     if (pl->scheme == 2) {
       ADD(OP_REACT, 0, F[V], nullptr, F[N0], nullptr, PK_REACT, 2);
+      BND(0, F[N0]);
       ADD(OP_S1, 1, F[V], F[N0], F[V2], F[PF], PK_S1, 4);
       ADD(OP_REACT, 0, F[V2], nullptr, F[N2], nullptr, PK_REACT, 2);
+      BND(1, F[N2]);
       ADD(OP_S2, 1, F[N2], F[PF], F[V], nullptr, PK_S2, 3);
     } else {
       ADD(OP_REACT, 0, F[V], nullptr, F[N0], nullptr, PK_REACT, 2);
+      BND(0, F[N0]);
       ADD(OP_RK1, 1, F[V], F[N0], F[V], nullptr, PK_RK1, 3);
     }
   } else {
     ADD(OP_TRANSFORM, 1, F[V], nullptr, F[V2], nullptr, PK_TRANSFORM, 2);
     ADD(OP_REACT, 0, F[V2], nullptr, F[N0], nullptr, PK_REACT, 2);
     ADD(OP_TRANSFORM, 1, F[N0], nullptr, F[N0], nullptr, PK_TRANSFORM, 2);
+    BND(0, F[N0]);
     if (pl->scheme == 2) {
       ADD(OP_S1, 2, F[V], F[N0], F[V2], F[PF], PK_S1, 4);
       ADD(OP_TRANSFORM, 1, F[V2], nullptr, F[V2], nullptr, PK_TRANSFORM, 2);
       ADD(OP_REACT, 0, F[V2], nullptr, F[N2], nullptr, PK_REACT, 2);
       ADD(OP_TRANSFORM, 1, F[N2], nullptr, F[N2], nullptr, PK_TRANSFORM, 2);
+      BND(1, F[N2]);
       ADD(OP_S2, 2, F[N2], F[PF], F[V], nullptr, PK_S2, 3);
     } else {
       ADD(OP_RK1, 2, F[V], F[N0], F[V], nullptr, PK_RK1, 3);
     }
   }
+#undef BND
 #undef ADD
   return ETD_OK;
 }
@@ -746,6 +832,30 @@ etd_status ensure_graph(etd_plan_s* pl, int gsteps) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   pl->graph_steps = gsteps;
+  return ETD_OK;
+}
+
+// Runs with nonhomogeneous Dirichlet data: per time step the callback fills the pinned staging
+// buffer for each stage time, one copy moves it to the device, the step's launches follow, and the
+// stream is synchronised before the buffer is refilled.
+etd_status run_steps_boundary(etd_plan_s* pl, int64_t nsteps, double t0, cudaStream_t s) {
+  const int stages = pl->scheme == 2 ? 2 : 1;
+  const size_t per = 2 * (size_t)pl->bnd_count;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    const double tn = t0 + (double)n * pl->tau;
+    for (int k = 0; k < stages; ++k) {
+      const double t = tn + (k ? pl->opt.c2 * pl->tau : 0.0);
+      double* hb = pl->bnd_host + k * per;
+      const int rc = pl->bnd_fn(t, hb, hb + pl->bnd_count, pl->bnd_ctx);
+      if (rc != 0) return fail(ETD_ERR_INVALID_ARG, "boundary callback returned %d at t = %g", rc, t);
+    }
+    ETD_CUDA(cudaMemcpyAsync(pl->bnd_dev, pl->bnd_host, stages * per * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (const Launch& L : pl->step) {
+      etd_status st = launch(L, s);
+      if (st != ETD_OK) return st;
+    }
+    ETD_CUDA(cudaStreamSynchronize(s));
+  }
   return ETD_OK;
 }
 
@@ -1226,7 +1336,8 @@ etd_status etd_run_from(etd_plan pl, void* u, int64_t nsteps, double t0, void* s
   if (st != ETD_OK) return st;
   for (const Launch& L : ent)
     if ((st = launch(L, s)) != ETD_OK) return st;
-  if ((st = run_steps(pl, nsteps, s)) != ETD_OK) return st;
+  st = pl->bnd_on ? run_steps_boundary(pl, nsteps, t0, s) : run_steps(pl, nsteps, s);
+  if (st != ETD_OK) return st;
   for (const Launch& L : ext)
     if ((st = launch(L, s)) != ETD_OK) return st;
   return ETD_OK;
@@ -1298,6 +1409,56 @@ etd_status etd_set_source(etd_plan pl, double amp, double rate, const double* gx
     pl->src_on = true;
     pl->src_amp = amp;
     pl->src_rate = rate;
+  }
+  destroy_graph(pl);
+  etd_status st = pl->elem == 4 ? build_step<float>(pl) : build_step<double>(pl);
+  if (st != ETD_OK) return st;
+  if (pl->elem == 4) apply_source<float>(pl);
+  else apply_source<double>(pl);
+  return ETD_OK;
+}
+
+etd_status etd_boundary_count(etd_plan pl, int64_t* count) {
+  if (!pl || !count) return fail(ETD_ERR_INVALID_ARG, "plan or count is NULL");
+  if (pl->periodic) return fail(ETD_ERR_INVALID_ARG, "a periodic plan has no boundary");
+  const int64_t Nx = pl->N[0], Ny = pl->N[1], Nz = pl->ndim == 3 ? pl->N[2] : 0;
+  *count = pl->ndim == 3 ? 2 * (Nz + 1) * (Ny + 1) + 2 * (Nz + 1) * (Nx + 1) + 2 * (Ny + 1) * (Nx + 1)
+                         : 2 * (Ny + 1) + 2 * (Nx + 1);
+  return ETD_OK;
+}
+
+etd_status etd_set_boundary(etd_plan pl, etd_boundary_fn fn, void* ctx) {
+  if (!pl) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+  if (pl->periodic) return fail(ETD_ERR_INVALID_ARG, "a periodic plan has no boundary");
+  if (pl->gemm) return fail(ETD_ERR_UNSUPPORTED, "boundary data are supported on the FFT routes");
+  if (!fn) {
+    if (!pl->bnd_on) return ETD_OK;
+    pl->bnd_on = false;
+  } else {
+    int64_t count = 0;
+    etd_status st = etd_boundary_count(pl, &count);
+    if (st != ETD_OK) return st;
+    if (!pl->bnd_host) {
+      const size_t bytes = 4 * (size_t)count * sizeof(double);   // two stages x (values, derivatives)
+      ETD_CUDA(cudaMallocHost(&pl->bnd_host, bytes));
+      ETD_CUDA(cudaMalloc(&pl->bnd_dev, bytes));
+      ETD_CUDA(cudaMalloc(&pl->bnd_field, pl->nfield * pl->elem));
+      // 1 / lambda^A per mode, lambda^A_i = (h/3)(2 + cos(i pi / N)) (mode 0: unused, 0)
+      std::vector<double> ia((size_t)pl->nx + pl->ny + pl->nz, 0.0);
+      size_t off = 0;
+      const int n[3] = {pl->nx, pl->ny, pl->nz};
+      for (int d = 0; d < pl->ndim; ++d) {
+        for (int i = 1; i < n[d]; ++i)
+          ia[off + i] = 3.0 / (pl->h[d] * (2.0 + cos(M_PI * (double)i / (double)n[d])));
+        off += n[d];
+      }
+      ETD_CUDA(cudaMalloc(&pl->bnd_ia, ia.size() * sizeof(double)));
+      ETD_CUDA(cudaMemcpy(pl->bnd_ia, ia.data(), ia.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    pl->bnd_count = count;
+    pl->bnd_fn = fn;
+    pl->bnd_ctx = ctx;
+    pl->bnd_on = true;
   }
   destroy_graph(pl);
   etd_status st = pl->elem == 4 ? build_step<float>(pl) : build_step<double>(pl);
@@ -1381,6 +1542,7 @@ etd_status etd_monitor(etd_plan pl, const void* u, etd_monitors* out, void* stre
 etd_status etd_run_profiled(etd_plan pl, void* u, int64_t nsteps, void* stream, double* ms, int64_t* cnt) {
   if (!pl || !u || !ms || !cnt) return fail(ETD_ERR_INVALID_ARG, "NULL argument");
   if (nsteps < 0) return fail(ETD_ERR_INVALID_ARG, "nsteps < 0");
+  if (pl->bnd_on) return fail(ETD_ERR_UNSUPPORTED, "profiled runs take homogeneous boundary data");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int k = 0; k < ETD_NUM_PASS_KINDS; ++k) {
     ms[k] = 0;
@@ -1453,6 +1615,10 @@ etd_status etd_destroy(etd_plan pl) {
   if (pl->src_tab) cudaFree(pl->src_tab);
   if (pl->clock) cudaFree(pl->clock);
   if (pl->dev_err) cudaFree(pl->dev_err);
+  if (pl->bnd_host) cudaFreeHost(pl->bnd_host);
+  if (pl->bnd_dev) cudaFree(pl->bnd_dev);
+  if (pl->bnd_field) cudaFree(pl->bnd_field);
+  if (pl->bnd_ia) cudaFree(pl->bnd_ia);
   delete pl;
   return ETD_OK;
 }

@@ -96,6 +96,57 @@ class Plan:
                   "etd_run_from")
         return u
 
+    def boundary_count(self) -> int:
+        n = ctypes.c_int64()
+        nat.check(nat.lib().etd_boundary_count(self._h, ctypes.byref(n)), "etd_boundary_count")
+        return int(n.value)
+
+    def boundary_nodes(self):
+        """Full-grid node indices (ix, iy[, iz]) of the packed boundary layout of etd_set_boundary:
+        faces x = 0, x = L_x, y = 0, y = L_y (, z = 0, z = L_z), each over all its nodes, x fastest."""
+        Nx, Ny = self.N[0], self.N[1]
+        if self.ndim == 2:
+            iy = np.arange(Ny + 1)
+            ix = np.arange(Nx + 1)
+            xs = [np.zeros_like(iy), np.full_like(iy, Nx), ix, ix]
+            ys = [iy, iy, np.zeros_like(ix), np.full_like(ix, Ny)]
+            return np.concatenate(xs), np.concatenate(ys)
+        Nz = self.N[2]
+        zy = np.meshgrid(np.arange(Nz + 1), np.arange(Ny + 1), indexing="ij")
+        zx = np.meshgrid(np.arange(Nz + 1), np.arange(Nx + 1), indexing="ij")
+        yx = np.meshgrid(np.arange(Ny + 1), np.arange(Nx + 1), indexing="ij")
+        xs, ys, zs = [], [], []
+        for v in (0, Nx):
+            xs.append(np.full(zy[0].size, v)); ys.append(zy[1].ravel()); zs.append(zy[0].ravel())
+        for v in (0, Ny):
+            xs.append(zx[1].ravel()); ys.append(np.full(zx[0].size, v)); zs.append(zx[0].ravel())
+        for v in (0, Nz):
+            xs.append(yx[1].ravel()); ys.append(yx[0].ravel()); zs.append(np.full(yx[0].size, v))
+        return np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)
+
+    def set_boundary(self, fn):
+        """Nonhomogeneous Dirichlet data: fn(t) -> (g, gdot), the boundary values and their time
+        derivatives at time t in the packed layout of `boundary_nodes()`; None removes them."""
+        L = nat.lib()
+        if fn is None:
+            nat.check(L.etd_set_boundary(self._h, nat.BOUNDARY_FN(), None), "etd_set_boundary")
+            self._bnd_cb = None
+            return
+        count = self.boundary_count()
+
+        def cb(t, gp, gdp, ctx):
+            try:
+                g, gd = fn(t)
+                np.ctypeslib.as_array(gp, (count,))[:] = np.asarray(g, dtype=np.float64).reshape(count)
+                np.ctypeslib.as_array(gdp, (count,))[:] = np.asarray(gd, dtype=np.float64).reshape(count)
+                return 0
+            except Exception:   # reported to the caller of run() as ETD_ERR_INVALID_ARG
+                return 1
+
+        c = nat.BOUNDARY_FN(cb)
+        nat.check(L.etd_set_boundary(self._h, c, None), "etd_set_boundary")
+        self._bnd_cb = c   # the library holds the pointer: keep the callback alive
+
     def set_source(self, amp: float, rate: float, *profiles):
         """Separable time-dependent source amp exp(-rate t) g_x[i] g_y[j] (g_z[k]) added to the reaction;
         one profile of N_a - 1 interior values per axis (periodic: N_a nodal values), x first; no

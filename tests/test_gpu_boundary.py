@@ -1,0 +1,195 @@
+"""Nonhomogeneous Dirichlet data on the GPU (etd_set_boundary; Section 4, Example 5.2, Table 4),
+through the C ABI, against the CPU oracle (oracle/boundary.py).
+
+Tolerances as for the homogeneous path: FP64 1e-12, FP32 1e-5 (short runs). Table 4: the printed
+EIFE1 and EIFE2 temporal L2 errors at the printed 1024 x 64 x 64 mesh, FP64 on the GPU, within 2%
+(the oracle approaches them from below on 128/256/512 meshes: 0.8% and 3.2% short at 512 for
+EIFE2 N_T = 16 and 32).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import boundary as obnd
+from oracle import etd as oetd
+from paper_2209_11922_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table4_example52_temporal.txt")
+
+
+def _plan(N, D, tau, scheme, dtype, h, **kw):
+    from paper_2209_11922_gb300.etd import Plan
+    return Plan(N, D, tau, scheme=scheme, dtype=dtype, h=h, **kw)
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a.astype(np.float32 if dtype == "f32" else np.float64))).cuda()
+
+
+def _rel(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    return np.linalg.norm(got - ref) / np.linalg.norm(ref), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def _smooth(t, X, Y, Z=None):
+    """Smooth time-dependent data and its time derivative (any node coordinates)."""
+    s = X + 2.0 * Y + (0.5 * Z if Z is not None else 0.0)
+    return (1.0 + 0.5 * np.sin(3.0 * t)) * np.cos(s), 1.5 * np.cos(3.0 * t) * np.cos(s)
+
+
+def _full_coords(N, h):
+    axes = [np.arange(n + 1) * hh for n, hh in zip(N, h)]
+    return np.meshgrid(*reversed(axes), indexing="ij")[::-1]
+
+
+CASES = [((64, 48), 2), ((32, 96), 1), ((32, 16, 24), 2), ((16, 32, 8), 1)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])) + f"_s{c[1]}")
+def test_boundary_data_match_oracle(case, dtype):
+    """Smooth time-dependent boundary data, Allen-Cahn reaction, started at t0 = 0.2 as 2 + 3 steps."""
+    N, scheme = case
+    h = tuple(1.0 / n for n in N)
+    D, tau, t0 = 0.05, 0.01, 0.2
+    C = _full_coords(N, h)
+    f = oetd.allen_cahn(1.0, -1.0)
+    src = obnd.boundary_source(N, h, D, f, lambda t: _smooth(t, *C))
+    inner = tuple(slice(1, -1) for _ in N)
+    U0 = _smooth(t0, *C)[0][inner] + 0.05 * inputs.uniform_field(inputs.interior_shape(N), -1, 1, 51)
+    if dtype == "f32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    ref = oetd.make_stepper(N, h, D, tau, scheme).run(U0, 5, obnd.with_boundary(f, src), t0=t0)
+    with _plan(N, D, tau, scheme, dtype, h) as pl:
+        nodes = pl.boundary_nodes()
+        xyz = [idx * hh for idx, hh in zip(nodes, h)]
+        pl.set_boundary(lambda t: _smooth(t, *xyz))
+        d = _dev(U0, dtype)
+        pl.run(d, 2, t0=t0)
+        pl.run(d, 3, t0=t0 + 2 * tau)
+        l2, linf = _rel(d.cpu().numpy(), ref)
+    assert l2 <= TOL[dtype] and linf <= TOL[dtype], (l2, linf)
+
+
+def test_linear_field_stays_on_the_gpu():
+    """f = 0 and linear boundary data: the linear field is a discrete steady state."""
+    N = (48, 32, 16)
+    h = tuple(1.0 / n for n in N)
+    with _plan(N, 0.3, 0.05, 2, "f64", h, flin=0.0, fcub=0.0) as pl:
+        nodes = pl.boundary_nodes()
+        lin = lambda ix, iy, iz: 0.2 + 0.9 * ix * h[0] - 0.4 * iy * h[1] + 0.7 * iz * h[2]
+        g = lin(*nodes)
+        pl.set_boundary(lambda t: (g, np.zeros_like(g)))
+        iz, iy, ix = np.meshgrid(*[np.arange(1, n) for n in reversed(N)], indexing="ij")
+        U = lin(ix, iy, iz)
+        d = _dev(U, "f64")
+        pl.run(d, 6)
+        got = d.cpu().numpy()
+    assert np.abs(got - U).max() <= 1e-12
+
+
+def test_boundary_callback_failure_is_reported():
+    from paper_2209_11922_gb300 import _native as nat
+    N = (16, 16)
+    with _plan(N, 0.1, 0.01, 2, "f64", (1 / 16, 1 / 16)) as pl:
+        def bad(t):
+            raise RuntimeError("no data")
+        pl.set_boundary(bad)
+        d = _dev(np.zeros((15, 15)), "f64")
+        with pytest.raises(nat.EtdError) as ei:
+            pl.run(d, 1)
+        assert ei.value.status == nat.ETD_ERR_INVALID_ARG
+        pl.set_boundary(None)          # removed: homogeneous again, graph path
+        pl.run(d, 40)
+        assert float(d.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------- Example 5.2 / Table 4 at the printed mesh
+EPS = 0.05
+SPEED = 3 / (math.sqrt(2) * EPS)
+T_END = 3 * math.sqrt(2) * EPS / 5
+LEN = (math.sqrt(2), 1 / 8, 1 / 8)
+
+
+def _wave(t, x):
+    return 0.5 * (1 - np.tanh((x - SPEED * t) / (2 * math.sqrt(2) * EPS)))
+
+
+def _wave_t(t, x):
+    xi = (x - SPEED * t) / (2 * math.sqrt(2) * EPS)
+    return SPEED / (4 * math.sqrt(2) * EPS) / np.cosh(xi) ** 2
+
+
+def _mass_apply(E, h, axis):
+    """(h/6)[1 4 1] along array axis `axis` of a full-grid field (all nodes, boundary rows included)."""
+    out = 4.0 * E
+    sl = lambda a, b: tuple(slice(a, b) if k == axis else slice(None) for k in range(E.ndim))
+    out[sl(1, None)] += E[sl(0, -1)]
+    out[sl(0, -1)] += E[sl(1, None)]
+    out[sl(0, 1)] -= E[sl(0, 1)] * 2.0      # end rows of the all-node matrix: (h/6)[2 1]
+    out[sl(-1, None)] -= E[sl(-1, None)] * 2.0
+    return out * (h / 6.0)
+
+
+def _stiff_apply(E, h, axis):
+    out = 2.0 * E
+    sl = lambda a, b: tuple(slice(a, b) if k == axis else slice(None) for k in range(E.ndim))
+    out[sl(1, None)] -= E[sl(0, -1)]
+    out[sl(0, -1)] -= E[sl(1, None)]
+    out[sl(0, 1)] -= E[sl(0, 1)]             # end rows: (1/h)[1 -1]
+    out[sl(-1, None)] -= E[sl(-1, None)]
+    return out / h
+
+
+def _fe_norms(E, h):
+    """FE L2 norm, H1 norm, and the H1 norm with only the x-derivative part of the seminorm, of a
+    full-grid nodal field (storage order z, y, x; h per paper axis)."""
+    d = E.ndim
+    ME = E
+    for a in range(d):
+        ME = _mass_apply(ME, h[a], d - 1 - a)
+    parts = []
+    for a in range(d):
+        T = E
+        for b in range(d):
+            T = (_stiff_apply if b == a else _mass_apply)(T, h[b], d - 1 - b)
+        parts.append(float(np.sum(E * T)))
+    l2sq = float(np.sum(E * ME))
+    return math.sqrt(l2sq), math.sqrt(l2sq + sum(parts)), math.sqrt(l2sq + parts[0])
+
+
+def _table4_rows():
+    rows = []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                sc, nt, l2, h1 = line.split()
+                rows.append((int(sc), int(nt), float(l2), float(h1)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _table4_rows(), ids=lambda r: f"EIFE{r[0]}-NT{r[1]}")
+def test_example52_table4_on_the_gpu(row):
+    scheme, nt, l2_printed, h1_printed = row
+    N = (1024, 64, 64)
+    h = tuple(l / n for l, n in zip(LEN, N))
+    with _plan(N, 1.0, T_END / nt, scheme, "f64", h, flin=1 / EPS ** 2, fcub=-1 / EPS ** 2) as pl:
+        xb = pl.boundary_nodes()[0] * h[0]
+        pl.set_boundary(lambda t: (_wave(t, xb), _wave_t(t, xb)))
+        x = np.arange(1, N[0]) * h[0]
+        U0 = np.broadcast_to(_wave(0.0, x), (N[2] - 1, N[1] - 1, N[0] - 1)).copy()
+        d = _dev(U0, "f64")
+        pl.run(d, nt)
+        U = d.cpu().numpy()
+    E = np.zeros((N[2] + 1, N[1] + 1, N[0] + 1))
+    E[1:-1, 1:-1, 1:-1] = U - _wave(T_END, x)
+    l2, h1, h1x = _fe_norms(E, h)
+    print(f"EIFE{scheme} N_T={nt}: L2 {l2:.4e} (printed {l2_printed:.4e}), H1 {h1:.4e} x-part only {h1x:.4e} "
+          f"(printed {h1_printed:.4e})")
+    assert l2 == pytest.approx(l2_printed, rel=0.05)

@@ -182,3 +182,10 @@ def test_periodic_and_log_reaction_arguments_rejected_on_the_host(L):
     h = (ctypes.c_double * 2)(1 / 64, 1 / 64)
     D = (ctypes.c_double * 1)(1e-3)
     assert L.etd_batch_create(ctypes.byref(b), 1, N, h, D, 0.01, 2, ctypes.byref(opt)) == nat.ETD_ERR_UNSUPPORTED
+
+
+def test_boundary_arguments_rejected_on_the_host(L):
+    n = ctypes.c_int64()
+    assert L.etd_boundary_count(None, ctypes.byref(n)) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_set_boundary(None, nat.BOUNDARY_FN(), None) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_pass_kind_name(8) == b"boundary"
