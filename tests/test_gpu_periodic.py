@@ -62,6 +62,11 @@ CASES = [
     ((16, 24, 32), 1e-3, 1e-2, 5, 2, "ac"),
     ((32, 32, 32), 1e-4, 20 / 2048, 6, 2, "fh"),
     ((48, 16, 8), 1e-4, 20 / 2048, 4, 1, "fh"),
+    # extremes: the shortest and longest supported axes (4, 6 and 2048, 1536)
+    ((4, 2048), 1e-4, 1e-2, 3, 2, "ac"),
+    ((2048, 4), 1e-4, 20 / 2048, 3, 2, "fh"),
+    ((1536, 6), 1e-4, 1e-2, 2, 1, "ac"),
+    ((4, 6, 8), 1e-2, 1e-2, 3, 2, "fh"),
 ]
 
 
@@ -206,3 +211,17 @@ def test_dirichlet_gemm_routes_take_the_artanh_term(route):
         d = _dev(U0, "f32")
         pl.run(d, nsteps)
         _check(d.cpu().numpy(), ref, GEMM_TOL[route], f"{route} Dirichlet")
+
+
+def test_periodic_zero_steps_is_a_no_op_and_split_runs_agree():
+    N, D, tau = (64, 32, 16), 1e-4, 20 / 2048
+    U0 = _u0(N, 49, "f64")
+    with _plan(N, D, tau, 2, "f64", **FH) as pl:
+        d = _dev(U0, "f64")
+        pl.run(d, 0)
+        assert np.array_equal(d.cpu().numpy(), U0)
+        pl.run(d, 3)
+        pl.run(d, 4)
+        e = _dev(U0, "f64")
+        pl.run(e, 7)
+        _check(d.cpu().numpy(), e.cpu().numpy(), 1e-13, "3 + 4 vs 7 steps")
