@@ -92,8 +92,11 @@ class Plan:
 
     # ------------------------------------------------------------------ API
     def run(self, u, nsteps: int, stream=None, t0: float = 0.0):
-        nat.check(nat.lib().etd_run_from(self._h, self._check_field(u), int(nsteps), float(t0), _stream_ptr(stream)),
-                  "etd_run_from")
+        self._bnd_exc = None
+        st = nat.lib().etd_run_from(self._h, self._check_field(u), int(nsteps), float(t0), _stream_ptr(stream))
+        if st != nat.ETD_OK and getattr(self, "_bnd_exc", None) is not None:
+            raise nat.EtdError(st, "etd_run_from (boundary callback)") from self._bnd_exc
+        nat.check(st, "etd_run_from")
         return u
 
     def boundary_count(self) -> int:
@@ -140,7 +143,8 @@ class Plan:
                 np.ctypeslib.as_array(gp, (count,))[:] = np.asarray(g, dtype=np.float64).reshape(count)
                 np.ctypeslib.as_array(gdp, (count,))[:] = np.asarray(gd, dtype=np.float64).reshape(count)
                 return 0
-            except Exception:   # reported to the caller of run() as ETD_ERR_INVALID_ARG
+            except Exception as e:   # run() raises EtdError(ETD_ERR_INVALID_ARG) from it
+                self._bnd_exc = e
                 return 1
 
         c = nat.BOUNDARY_FN(cb)

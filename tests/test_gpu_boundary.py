@@ -105,6 +105,7 @@ def test_boundary_callback_failure_is_reported():
         with pytest.raises(nat.EtdError) as ei:
             pl.run(d, 1)
         assert ei.value.status == nat.ETD_ERR_INVALID_ARG
+        assert isinstance(ei.value.__cause__, RuntimeError) and "no data" in str(ei.value.__cause__)
         pl.set_boundary(None)          # removed: homogeneous again, graph path
         pl.run(d, 40)
         assert float(d.abs().max()) == 0.0
