@@ -2,6 +2,7 @@
 include/etd.h declares, and rejects invalid arguments before touching the device."""
 import ctypes
 
+import numpy as np
 import pytest
 
 from paper_2209_11922_gb300 import _native as nat
@@ -189,3 +190,30 @@ def test_boundary_arguments_rejected_on_the_host(L):
     assert L.etd_boundary_count(None, ctypes.byref(n)) == nat.ETD_ERR_INVALID_ARG
     assert L.etd_set_boundary(None, nat.BOUNDARY_FN(), None) == nat.ETD_ERR_INVALID_ARG
     assert L.etd_pass_kind_name(8) == b"boundary"
+
+
+@pytest.mark.parametrize("N", [(4, 6), (5, 3, 4)])
+def test_boundary_layout_matches_the_header(N):
+    """Plan.boundary_nodes() enumerates the faces in the order etd.h documents (x = 0, x = L_x, y = 0,
+    y = L_y, z = 0, z = L_z; all nodes of each face, x fastest) and matches etd_boundary_count's size."""
+    from paper_2209_11922_gb300.etd import Plan
+    pl = object.__new__(Plan)
+    pl.N, pl.ndim = tuple(N), len(N)
+    got = np.stack(pl.boundary_nodes(), axis=1)
+    want = []
+    if len(N) == 2:
+        Nx, Ny = N
+        want += [(0, j) for j in range(Ny + 1)] + [(Nx, j) for j in range(Ny + 1)]
+        want += [(i, 0) for i in range(Nx + 1)] + [(i, Ny) for i in range(Nx + 1)]
+        count = 2 * (Ny + 1) + 2 * (Nx + 1)
+    else:
+        Nx, Ny, Nz = N
+        for v in (0, Nx):
+            want += [(v, j, k) for k in range(Nz + 1) for j in range(Ny + 1)]
+        for v in (0, Ny):
+            want += [(i, v, k) for k in range(Nz + 1) for i in range(Nx + 1)]
+        for v in (0, Nz):
+            want += [(i, j, v) for j in range(Ny + 1) for i in range(Nx + 1)]
+        count = 2 * (Nz + 1) * (Ny + 1) + 2 * (Nz + 1) * (Nx + 1) + 2 * (Ny + 1) * (Nx + 1)
+    assert got.shape[0] == count
+    assert [tuple(r) for r in got] == want
