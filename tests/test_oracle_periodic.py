@@ -269,3 +269,15 @@ def test_hartley_matrix_is_the_real_form_of_the_dft(N):
     th = 2 * np.pi * np.arange(N) / N
     np.testing.assert_allclose(H @ A @ H, np.diag((2 + np.cos(th)) / (3 * N)), atol=1e-14)
     np.testing.assert_allclose(H @ B @ H, np.diag(2 * N * (1 - np.cos(th))), atol=1e-10)
+
+
+def test_double_well_energy_is_the_allen_cahn_potential():
+    """The monitors' default potential is pinned by the reaction it belongs to: on constant periodic
+    fields (no gradient term) dE/du = -(u - u^3) per unit volume, and E vanishes in the wells u = +-1."""
+    N, h = (6, 5, 4), (1 / 6, 0.2, 0.25)
+    vol = np.prod(h) * np.prod(N)
+    e = lambda v: monitors.monitors(np.full((4, 5, 6), v), N, h, 0.3, "periodic")["energy"]
+    for c in (-0.7, 0.2, 0.55, 1.3):
+        d = 1e-5
+        assert (e(c + d) - e(c - d)) / (2 * d) / vol == pytest.approx(-(c - c ** 3), rel=1e-7, abs=1e-10)
+    assert e(1.0) == pytest.approx(0.0, abs=1e-15) and e(-1.0) == pytest.approx(0.0, abs=1e-15)
