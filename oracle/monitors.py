@@ -4,8 +4,9 @@
            Kronecker structure of eq. (4.1), which the tests pin against global assembly).
 * energy = 1/2 U^T K U + sum over interior nodes of prod_a h_a * (u^2 - 1)^2 / 4; the paper states an
            energy only for the Flory-Huggins case (Section 5.2), so this lumped double-well form is
-           a reading for f = u - u^3 and is used as a monitor only (parity unpinned for its
-           potential term; the quadratic term is pinned through K).
+           a reading for f = u - u^3 and is used as a monitor only (the quadratic term is pinned
+           through K, the potential through its reaction: dE/du = -f on constant periodic fields,
+           zero in the wells).
 * maxabs = max |u|, the quantity of the maximum bound principle discussed in Sections 1 and 5.2.
 
 With ``flory_huggins=(theta, theta_c)`` the potential term is that of the energy functional stated
