@@ -94,8 +94,8 @@ typedef struct {
                         invalid. Tests the failure path; any other value is ignored. */
   int bc;            /* boundary condition of every axis: ETD_BC_DIRICHLET (default) or ETD_BC_PERIODIC */
   double flog;       /* coefficient of artanh(u) = (1/2) ln((1+u)/(1-u)) in f; default 0. Nonzero values
-                        run on periodic plans (any route) and on the GEMM routes; a Dirichlet plan on
-                        an FFT route and batches return ETD_ERR_UNSUPPORTED. Where it is nonzero the
+                        run on periodic plans and batches (any route) and on the GEMM routes; a Dirichlet
+                        plan on an FFT route or a Dirichlet batch returns ETD_ERR_UNSUPPORTED. Where it is nonzero the
                         field must stay in (-1, 1) (|u| >= 1 gives non-finite values, which
                         etd_monitor reports). */
 } etd_options;
@@ -264,15 +264,16 @@ etd_status etd_destroy(etd_plan plan);
  * (the batched kernel is a separate instantiation, so the compiler may contract and order the
  * floating-point operations differently; measured differences are at the dtype's rounding level).
  * Allocates per-problem fields and tables on the current device. Errors as for etd_plan_create;
- * count <= 0 is ETD_ERR_INVALID_ARG; the GEMM routes and periodic boundaries are
- * ETD_ERR_UNSUPPORTED for batches.
+ * count <= 0 is ETD_ERR_INVALID_ARG; the GEMM routes are ETD_ERR_UNSUPPORTED for batches. With
+ * opt->bc = ETD_BC_PERIODIC every problem is periodic (fields [N_y][N_x]) and flog may be nonzero;
+ * Dirichlet batches take flog = 0.
  */
 typedef struct etd_batch_s* etd_batch;
 etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const double* h, const double* D,
                             double tau, etd_scheme scheme, const etd_options* opt);
 
 /* Advance every problem by nsteps >= 0 steps: u is a HOST array of `count` DEVICE pointers, u[i] the
- * dense field of problem i (shape [N[2i+1]-1][N[2i]-1], updated in place). Asynchronous on stream;
+ * dense field of problem i (shape [N[2i+1]-1][N[2i]-1], periodic [N[2i+1]][N[2i]], updated in place). Asynchronous on stream;
  * the pointer array itself may be reused as soon as the call returns. */
 etd_status etd_batch_run(etd_batch b, void* const* u, int64_t nsteps, void* stream);
 

@@ -903,6 +903,7 @@ struct BatchGroup {
 
 struct etd_batch_s {
   int count = 0, elem = 4, scheme = 2;
+  int periodic = 0;                // every problem periodic (Hartley kernels), else homogeneous Dirichlet
   etd_options opt{};
   double tau = 0;
   int device = 0, num_sms = 148, optin = 0;
@@ -1042,7 +1043,8 @@ etd_status batch_build_op(etd_batch_s* b, const std::vector<BatchTables>& tabs, 
     g.fn = k->fn_batched;
     g.tpp = k->tpp;
     long long unk = 0;
-    for (int i : g.inst) unk += (long long)(b->nx[i] - 1) * (b->ny[i] - 1);
+    const int cut = b->periodic ? 0 : 1;
+    for (int i : g.inst) unk += (long long)(b->nx[i] - cut) * (b->ny[i] - cut);
     g.alg_bytes = o.rw * (double)unk * sizeof(T);
     {
       cudaError_t e = cudaFuncSetAttribute(g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b->optin);
@@ -1118,8 +1120,8 @@ etd_status batch_build(etd_batch_s* b) {
     for (int a = 0; a < 2; ++a) {
       const KernelInfo* k = find_pass_kernel((int)sizeof(T), n[a], odd[a]);
       if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", n[a]);
-      append_axis_tables<T>(k, n[a], hh[a], b->tau * b->Dv[i], b->opt.c2, h, tabs[i].off[a]);
-      tabs[i].sc[a] = 0.5 * sqrt(2.0 / (double)n[a]);
+      append_axis_tables<T>(k, n[a], hh[a], b->tau * b->Dv[i], b->opt.c2, h, tabs[i].off[a], b->periodic != 0);
+      tabs[i].sc[a] = b->periodic ? 0.5 / sqrt((double)n[a]) : 0.5 * sqrt(2.0 / (double)n[a]);
     }
   }
   ETD_CUDA(cudaMalloc(&b->tables, h.size() * sizeof(T)));
@@ -1131,7 +1133,8 @@ etd_status batch_build(etd_batch_s* b) {
     b->field_off[i] = total;
     total += 5 * (size_t)b->nx[i] * b->ny[i];
     total = (total + 63) & ~(size_t)63;   // 256-byte aligned fields
-    b->unknowns += (int64_t)(b->nx[i] - 1) * (b->ny[i] - 1);
+    const int cut = b->periodic ? 0 : 1;
+    b->unknowns += (int64_t)(b->nx[i] - cut) * (b->ny[i] - cut);
   }
   b->ws_bytes = total * sizeof(T);
   cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
@@ -1650,9 +1653,10 @@ etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const d
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
   const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
   if (gemm) return fail(ETD_ERR_UNSUPPORTED, "batches run the FFT routes only");
-  if (o.bc != ETD_BC_DIRICHLET) return fail(ETD_ERR_UNSUPPORTED, "batches take Dirichlet boundaries only");
+  if (o.bc != ETD_BC_DIRICHLET && o.bc != ETD_BC_PERIODIC) return fail(ETD_ERR_INVALID_ARG, "unknown boundary condition");
   if (!std::isfinite(o.flog)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
-  if (o.flog != 0.0) return fail(ETD_ERR_UNSUPPORTED, "batches take the polynomial reaction only (flog = 0)");
+  if (o.flog != 0.0 && o.bc != ETD_BC_PERIODIC)
+    return fail(ETD_ERR_UNSUPPORTED, "the artanh reaction term runs on periodic batches only");
   for (int i = 0; i < count; ++i) {
     for (int a = 0; a < 2; ++a) {
       const int64_t n = N[2 * i + a];
@@ -1666,6 +1670,7 @@ etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const d
   b->count = count;
   b->scheme = scheme;
   b->opt = o;
+  b->periodic = o.bc == ETD_BC_PERIODIC;
   b->tau = tau;
   b->elem = o.dtype == ETD_F32 ? 4 : 8;
   for (int i = 0; i < count; ++i) {
@@ -1674,7 +1679,10 @@ etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const d
     b->hx.push_back(h[2 * i]);
     b->hy.push_back(h[2 * i + 1]);
     b->Dv.push_back(D[i]);
-    auto odd_of = [&](int64_t n) { return (o.dtype != ETD_F32 || o.route == ETD_ROUTE_FFT_HALF) ? 0 : (o.route == ETD_ROUTE_FFT ? 1 : (n >= 512 ? 1 : 0)); };
+    auto odd_of = [&](int64_t n) {
+      if (o.bc == ETD_BC_PERIODIC) return (int)V_HART;
+      return (o.dtype != ETD_F32 || o.route == ETD_ROUTE_FFT_HALF) ? 0 : (o.route == ETD_ROUTE_FFT ? 1 : (n >= 512 ? 1 : 0));
+    };
     b->oddx.push_back(odd_of(N[2 * i]));
     b->oddy.push_back(odd_of(N[2 * i + 1]));
   }

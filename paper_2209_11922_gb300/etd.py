@@ -235,11 +235,12 @@ class Plan:
 class Batch:
     """Many independent 2D problems advanced together (etd_batch_*): per problem its own
     intervals N_i = (N_x, N_y), mesh sizes (default 1/N) and diffusion D_i; common tau, scheme and
-    options. Fields are a list of CUDA tensors of shape (N_y - 1, N_x - 1)."""
+    options. Fields are a list of CUDA tensors of shape (N_y - 1, N_x - 1) (periodic: (N_y, N_x))."""
 
     def __init__(self, N: Sequence[Sequence[int]], D: Sequence[float], tau: float, scheme: int = 2,
                  dtype: str = "f32", h: Optional[Sequence[Sequence[float]]] = None, c2: float = 0.5,
-                 flin: float = 1.0, fcub: float = -1.0, route: str = "auto"):
+                 flin: float = 1.0, fcub: float = -1.0, route: str = "auto", bc: str = "dirichlet",
+                 flog: float = 0.0):
         L = nat.lib()
         self.N = [tuple(int(v) for v in n) for n in N]
         self.count = len(self.N)
@@ -251,7 +252,11 @@ class Batch:
         opt = nat.EtdOptions()
         L.etd_options_default(ctypes.byref(opt))
         opt.dtype, opt.route = _DT[dtype], _ROUTE[route]
-        opt.c2, opt.flin, opt.fcub = float(c2), float(flin), float(fcub)
+        opt.c2, opt.flin, opt.fcub, opt.flog = float(c2), float(flin), float(fcub), float(flog)
+        if bc not in _BC:
+            raise ValueError("bc must be 'dirichlet' or 'periodic'")
+        opt.bc = _BC[bc]
+        self.bc = bc
         Na = (ctypes.c_int64 * (2 * self.count))(*[v for n in self.N for v in n])
         ha = (ctypes.c_double * (2 * self.count))(*[v for x in self.h for v in x])
         Da = (ctypes.c_double * self.count)(*self.D)
@@ -261,7 +266,8 @@ class Batch:
         self._h = handle
 
     def shapes(self):
-        return [(ny - 1, nx - 1) for nx, ny in self.N]
+        cut = 0 if self.bc == "periodic" else 1
+        return [(ny - cut, nx - cut) for nx, ny in self.N]
 
     def run(self, fields, nsteps: int, stream=None):
         torch = _torch()

@@ -73,3 +73,26 @@ def test_batch_run_twice_continues_and_zero_steps_is_noop():
         b.run(b_, 13)
     for x, y in zip(a, b_):   # split runs agree to rounding (one extra transform round trip)
         assert torch.allclose(x, y, rtol=0, atol=1e-12 * float(x.abs().max()))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_periodic_batch_matches_oracle(dtype):
+    """A periodic batch (Hartley kernels) with the Flory-Huggins reaction of Example 5.3, problems of
+    uneven size, against the oracle's periodic path."""
+    from paper_2209_11922_gb300.etd import Batch
+    probs = [((96, 64), 1e-4), ((64, 128), 1e-3), ((384, 96), 1e-4), ((6, 48), 2e-3)]
+    tau, nsteps = 20 / 2048, 8
+    fh = dict(flin=1.6, fcub=0.0, flog=-0.8)
+    U0 = [inputs.uniform_field((ny, nx), -0.9, 0.9, seed=950 + i) for i, ((nx, ny), _) in enumerate(probs)]
+    if dtype == "f32":
+        U0 = [u.astype(np.float32).astype(np.float64) for u in U0]
+    fields = [torch.from_numpy(u.astype(np.float32 if dtype == "f32" else np.float64)).cuda() for u in U0]
+    with Batch([p[0] for p in probs], [p[1] for p in probs], tau, 2, dtype, bc="periodic", **fh) as b:
+        b.run(fields, nsteps)
+    tol = 1e-5 if dtype == "f32" else 1e-12
+    for (N, D), u0, f in zip(probs, U0, fields):
+        ref = oetd.run(u0, N, (1 / N[0], 1 / N[1]), D, tau, nsteps, 2, bc="periodic", **fh)
+        got = f.cpu().numpy().astype(np.float64)
+        l2 = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        linf = np.abs(got - ref).max() / np.abs(ref).max()
+        assert l2 <= tol and linf <= tol, (N, l2, linf)

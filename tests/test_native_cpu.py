@@ -182,7 +182,11 @@ def test_periodic_and_log_reaction_arguments_rejected_on_the_host(L):
     N = (ctypes.c_int64 * 2)(64, 64)
     h = (ctypes.c_double * 2)(1 / 64, 1 / 64)
     D = (ctypes.c_double * 1)(1e-3)
+    opt = _opts(L, nat.ETD_F32)
+    opt.flog = -0.8                     # Dirichlet batches take the polynomial reaction only
     assert L.etd_batch_create(ctypes.byref(b), 1, N, h, D, 0.01, 2, ctypes.byref(opt)) == nat.ETD_ERR_UNSUPPORTED
+    opt.bc = 7
+    assert L.etd_batch_create(ctypes.byref(b), 1, N, h, D, 0.01, 2, ctypes.byref(opt)) == nat.ETD_ERR_INVALID_ARG
 
 
 def test_boundary_arguments_rejected_on_the_host(L):
