@@ -154,7 +154,9 @@ etd_status etd_run_from(etd_plan plan, void* u, int64_t nsteps, double t0, void*
  * scheme as part of f; Example 5.2 of Section 5). The Galerkin system on all nodes with the boundary
  * nodal values g(t) prescribed has the interior rows
  *   M_II U' + K_II U = M_II f(U) + b(t),  b(t) = M_IB (f(g) - g'(t)) - K_IB g(t)
- * (the reaction taken on nodal values of every node), so each stage adds M_II^{-1} b(t) to the nodal
+ * (the reaction taken on nodal values of every node: flin g + fcub g^3 at the boundary nodes; a source
+ * set with etd_set_source is defined by its interior profiles and does not enter b), so each stage adds
+ * M_II^{-1} b(t) to the nodal
  * reaction: b is assembled on the GPU from the boundary values by the Q1 stencils, transformed along
  * every axis, scaled by the inverse mass eigenvalues and transformed back along the last axis.
  * `fn` supplies the data: fn(t, g, gdot, ctx) writes the boundary values and their time derivatives
