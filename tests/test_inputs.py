@@ -1,5 +1,6 @@
 """The seeded generator against the published SplitMix64 definition and its known first outputs."""
 import numpy as np
+import pytest
 
 from paper_2209_11922_gb300 import inputs
 
@@ -36,3 +37,20 @@ def test_uniform_field_range_and_shape():
     assert u.min() >= -0.9 and u.max() < 0.9
     w = inputs.AC2D_1024
     assert inputs.interior_shape(w.N) == (1023, 1023) and w.unknowns == 1023 * 1023
+
+
+def test_field_shapes_and_workload_sizes():
+    from paper_2209_11922_gb300 import inputs
+    assert inputs.field_shape((8, 6), "dirichlet") == (5, 7)
+    assert inputs.field_shape((8, 6), "periodic") == (6, 8)
+    assert inputs.field_shape((8, 6, 4), "periodic") == (4, 6, 8)
+    with pytest.raises(ValueError):
+        inputs.field_shape((8, 6), "neumann")
+    w = inputs.GC3D_128
+    assert w.bc == "periodic" and w.shape == (128, 128, 128) and w.unknowns == 128 ** 3
+    assert (w.flin, w.fcub, w.flog) == (1.6, 0.0, -0.8) and w.D == pytest.approx(0.01 ** 2)
+    assert w.tau * w.nsteps == pytest.approx(20.0)       # Example 5.3: T = 20, N_T = 2048
+    u = w.u0()
+    assert u.shape == w.shape and u.min() >= -0.9 and u.max() < 0.9
+    a = inputs.AC2D_1024
+    assert a.bc == "dirichlet" and a.unknowns == 1023 ** 2 and a.u0().shape == (1023, 1023)
