@@ -63,6 +63,12 @@ extern "C" etd_status etd_monitor_noalloc(int ndim, const int64_t* N, const doub
       if (!(std::isfinite(h[a]) && h[a] > 0)) return noalloc_fail(ETD_ERR_INVALID_ARG, "h[%d] must be finite and > 0", a);
       g.m[a] = (int)(N[a] - 1);
       g.h[a] = h[a];
+      // reject before multiplying: n * (N[a] - 1) never exceeds the maximum, so it cannot overflow
+      if (N[a] - 1 > (long long)ETD_MONITOR_NOALLOC_MAX_UNKNOWNS / n)
+        return noalloc_fail(ETD_ERR_INVALID_ARG,
+                            "more than the maximum of %d unknowns for etd_monitor_noalloc (its fixed scratch "
+                            "holds %d partial records); use etd_monitor with a plan",
+                            ETD_MONITOR_NOALLOC_MAX_UNKNOWNS, kMaxRecords);
       n *= (N[a] - 1);
     } else {
       g.m[a] = 1;
@@ -74,11 +80,6 @@ extern "C" etd_status etd_monitor_noalloc(int ndim, const int64_t* N, const doub
   g.flin = 1.0;
   g.fcub = -1.0;
   g.flog = 0.0;
-  if (n > (long long)ETD_MONITOR_NOALLOC_MAX_UNKNOWNS)
-    return noalloc_fail(ETD_ERR_INVALID_ARG,
-                        "%lld unknowns exceed the maximum of %d for etd_monitor_noalloc (its fixed scratch holds "
-                        "%d partial records); use etd_monitor with a plan",
-                        n, ETD_MONITOR_NOALLOC_MAX_UNKNOWNS, kMaxRecords);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(ETD_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
@@ -95,7 +96,7 @@ extern "C" etd_status etd_monitor_noalloc(int ndim, const int64_t* N, const doub
     }
     base = g_scratch_addr[dev];
   }
-  const int blocks = (int)((n + 2047) / 2048);   // <= kMaxRecords by the check above
+  const int blocks = (int)((n + 2047) / 2048);   // <= kMaxRecords by the per-axis checks above
   double* part = static_cast<double*>(base);
   long long* bad = reinterpret_cast<long long*>(part + 4 * (size_t)kMaxRecords);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

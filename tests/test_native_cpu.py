@@ -221,3 +221,15 @@ def test_boundary_layout_matches_the_header(N):
         count = 2 * (Nz + 1) * (Ny + 1) + 2 * (Nz + 1) * (Nx + 1) + 2 * (Ny + 1) * (Nx + 1)
     assert got.shape[0] == count
     assert [tuple(r) for r in got] == want
+
+
+@pytest.mark.parametrize("N", [(2 ** 21 + 1, 2 ** 21 + 1, 2 ** 21 + 1), (2 ** 30, 2 ** 30, 2), (6000, 6000, 2)])
+def test_noalloc_monitor_rejects_oversize_without_overflow(L, N):
+    """The size check of etd_monitor_noalloc runs axis by axis before each multiply: three axes of
+    2^21 unknowns (2^63 in total, which wraps a 64-bit product) are rejected like any field above
+    the maximum, on the host, before any device work."""
+    Na = (ctypes.c_int64 * 3)(*N)
+    ha = (ctypes.c_double * 3)(1e-3, 1e-3, 1e-3)
+    dummy = ctypes.c_void_p(256)   # never dereferenced: the call fails in its argument checks
+    st = L.etd_monitor_noalloc(3, Na, ha, 0.1, nat.ETD_F32, dummy, dummy, None)
+    assert st == nat.ETD_ERR_INVALID_ARG and b"maximum" in L.etd_last_error()
