@@ -1,13 +1,18 @@
 """Tensor-core (GEMM) transform routes against the CPU oracle, through the C ABI.
 
-Tolerances come from the operand precision of each route. A transform y = S x with S and x each
-perturbed by a relative representation error u has relative error at most about 2u; the bound
-allowed below is 5 x 2u, with u the route's operand precision:
-  gemm_tf32    TF32 operands keep 10 stored mantissa bits, u = 2^-10 (truncation)   -> 1e-2
-  gemm_bf16x3  x = hi + lo and S = hi + lo in bf16 pairs, u = 2^-16, and the dropped
-               lo*lo product is of the same order                                  -> 1.5e-4
-These runs are short (<= 10 steps), over which diffusion damps rather than amplifies the
-per-transform errors.
+Tolerances come from the operand precision of each route.
+  gemm_tf32    TF32 operands keep 10 stored mantissa bits, u = 2^-10 (truncation). A transform
+               y = S x with S and x each carrying a relative error u has relative error about 2u;
+               the bound allows 5 x 2u = 9.8e-3 (measured 1.6e-3 to 2.8e-3).
+  gemm_bf16x3  x = hi + lo and S = hi + lo in bf16 pairs (8 significant bits each, rounded to
+               nearest): |x - hi| <= 2^-8 |x| and |x - hi - lo| <= 2^-8 |x - hi| <= 2^-16 |x|, and
+               the products keep hi*hi + hi*lo + lo*hi, dropping lo*lo (<= 2^-16 |x||s|). Each
+               transform therefore carries a worst-case relative error of about 2u, u = 2^-16, i.e.
+               3.05e-5, which is the bound (measured 9.0e-6 to 1.43e-5 over these runs: the
+               per-element errors are random in sign and diffusion damps rather than amplifies
+               them over these short runs, so the multi-step error stays below one transform's
+               worst case). A dropped hi*lo product would add 2^-8 relative error and fail it.
+These runs are short (<= 10 steps).
 """
 import numpy as np
 import pytest
@@ -19,7 +24,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 ROUTES = ("gemm_tf32", "gemm_bf16x3")
-TOL = {"gemm_tf32": 5 * 2 * 2.0 ** -10, "gemm_bf16x3": 1.5e-4}
+TOL = {"gemm_tf32": 5 * 2 * 2.0 ** -10, "gemm_bf16x3": 2 * 2.0 ** -16}
 
 
 def _plan(N, D, tau, scheme=2, route="gemm_tf32", **kw):

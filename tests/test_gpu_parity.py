@@ -15,11 +15,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
-# FP32 over horizons of ~100 steps: every step rounds the state to FP32 at the magnitude it has
-# then, while the solution norm of these decaying random fields falls ~20x; an ideal FP32 pipeline
-# (correctly rounded FFT transforms, FP32 state) already reaches 1.1e-5 (64^2, T = 1) and 9.3e-6
-# (1024^2, 100 steps) against the FP64 oracle, so the long-horizon FP32 bound is 3x that floor.
-TOL_F32_LONG = 3e-5
+# The half-length FP32 route (ETD_ROUTE_FFT_HALF) computes the odd DST outputs as prefix sums of N/2
+# FFT outputs, so its rounding grows like sqrt(N/2) eps per transform instead of log N eps; it is an
+# explicitly lower-accuracy route and keeps a bound three times the FP32 one. Every default FP32 run
+# (any horizon, including 100 steps at 1024^2) is held to 1e-5: the error budget of an FP32 pipeline
+# (tests/test_fp32_error_budget.py) leaves most of that bound to the transforms.
+TOL_F32_HALF = 3e-5
 
 
 def _plan(N, D, tau, scheme=2, dtype="f64", **kw):
@@ -106,7 +107,7 @@ def test_steps_match_oracle(case):
         U0 = U0.astype(np.float32).astype(np.float64)
     h = tuple(1.0 / n for n in N)
     ref = oetd.run(U0, N, h, D, tau, nsteps, scheme)
-    tol = TOL_F32_LONG if (dtype == "f32" and nsteps >= 50) else None
+    tol = None
     with _plan(N, D, tau, scheme=scheme, dtype=dtype) as pl:
         d = _to_dev(U0, dtype)
         pl.run(d, nsteps)
@@ -117,7 +118,7 @@ def test_steps_match_oracle(case):
 @pytest.mark.parametrize("N,nsteps", [((64, 64), 10), ((96, 48), 5), ((1024, 1024), 3), ((32, 24, 16), 4)])
 def test_half_length_fp32_route(N, nsteps):
     """ETD_ROUTE_FFT_HALF: the prefix-sum DST lets rounding grow like sqrt(N/2) eps per transform,
-    so it is held to the long-horizon FP32 bound."""
+    so it is held to its own, looser bound."""
     shape = tuple(n - 1 for n in reversed(N))
     U0 = inputs.uniform_field(shape, -0.9, 0.9, seed=77).astype(np.float32).astype(np.float64)
     h = tuple(1.0 / n for n in N)
@@ -125,7 +126,7 @@ def test_half_length_fp32_route(N, nsteps):
     with _plan(N, 1e-3, 1e-2, 2, "f32", route="fft_half") as pl:
         d = _to_dev(U0, "f32")
         pl.run(d, nsteps)
-        _check(d.cpu().numpy(), ref, "f32", "fft_half", TOL_F32_LONG)
+        _check(d.cpu().numpy(), ref, "f32", "fft_half", TOL_F32_HALF)
 
 
 def test_nonunit_mesh_and_reaction_options():
@@ -222,24 +223,66 @@ def test_full_size_2d_1024_first_steps(dtype, scheme):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_full_size_2d_1024_first_100_steps(dtype):
     """The first 100 ETDRK2 steps of the 1024^2 workload (T = 0.5) stay within the tolerance."""
-    _full_size(inputs.AC2D_1024, dtype, 100, 2, TOL_F32_LONG if dtype == "f32" else None)
+    _full_size(inputs.AC2D_1024, dtype, 100, 2)
 
 
 def test_full_size_3d_256_first_step():
     _full_size(inputs.AC3D_256, "f32", 1)
 
 
-def test_full_size_sine_mode_decays_exactly():
+def test_full_size_3d_256_first_5_steps():
+    """Five ETDRK2 steps of the 256^3 workload on the default FP32 route against the oracle."""
+    _full_size(inputs.AC3D_256, "f32", 5)
+
+
+def _mu1024(k):
+    t = k * np.pi / 1024
+    return 6 * 1024 ** 2 * (1 - np.cos(t)) / (2 + np.cos(t))
+
+
+@pytest.mark.parametrize("p,q,n", [(5, 40, 64), (37, 250, 64), (37, 600, 4)])
+def test_full_size_sine_mode_decays_exactly(p, q, n):
     """f = 0 at 1024^2: a product sine mode is an eigenvector of every pass; the run must give
-    exp(-n tau D (mu_p + mu_q)) times the mode (closed form of Section 4)."""
-    N, D, tau, n = (1024, 1024), 1e-4, 5e-3, 64
+    exp(-n tau D (mu_p + mu_q)) times the mode (closed form of Section 4). High modes decay by
+    orders of magnitude, so the error is measured relative to ||U0||: a transform that leaks the
+    mode's amplitude into other modes shows there whatever the decay."""
+    N, D, tau = (1024, 1024), 1e-4, 5e-3
     x = np.arange(1, 1024) / 1024
-    p, q = 5, 40          # total decay exp(-0.5): transform rounding in other modes stays below tolerance
     U0 = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x))
-    mu = lambda k: 6 * 1024 ** 2 * (1 - np.cos(k * np.pi / 1024)) / (2 + np.cos(k * np.pi / 1024))
-    ref = np.exp(-n * tau * D * (mu(p) + mu(q))) * U0
+    ref = np.exp(-n * tau * D * (_mu1024(p) + _mu1024(q))) * U0
+    n0 = np.linalg.norm(U0)
     for dtype in ("f64", "f32"):
         with _plan(N, D, tau, 2, dtype, flin=0.0, fcub=0.0) as pl:
             d = _to_dev(U0, dtype)
             pl.run(d, n)
-            _check(d.cpu().numpy(), ref, dtype, dtype)
+            got = d.cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(got - ref) / n0
+        assert err <= TOL[dtype], (dtype, p, q, err)
+        if p == 5:   # mild decay: the relative error of the decayed mode itself
+            _check(got, ref, dtype, dtype)
+
+
+@pytest.mark.parametrize("q", [40, 450, 900])
+def test_full_size_high_mode_linear_reaction_closed_form(q):
+    """f = kappa u at 1024^2 keeps a product sine mode an eigenvector, and EIFE2 multiplies it per
+    step by R = e^{-z} + kappa tau (phi1 - phi2/c2)(-z) + kappa tau (phi2/c2)(-z) (e^{-c2 z} +
+    c2 kappa tau phi1(-c2 z)), z = tau D (mu_p + mu_q) (eq. (2.14) for one mode). The modes pick
+    z < 1 (series branch of the kernels' phi evaluation) and z > 1 (closed-form branch); kappa tau =
+    -0.25 weights the phi terms as much as the exponential."""
+    N, D, tau, kappa, c2, n, p = (1024, 1024), 1e-4, 5e-3, -50.0, 0.5, 4, 37
+    x = np.arange(1, 1024) / 1024
+    U0 = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x))
+    z = tau * D * (_mu1024(p) + _mu1024(q))
+    e = np.expm1(-z)
+    phi1 = lambda w: np.expm1(w) / w
+    phi2 = lambda w: (np.expm1(w) - w) / (w * w)
+    k = kappa * tau
+    R = (1 + e) + k * (phi1(-z) - phi2(-z) / c2) + k * (phi2(-z) / c2) * (np.exp(-c2 * z) + c2 * k * phi1(-c2 * z))
+    ref = R ** n * U0
+    for dtype in ("f64", "f32"):
+        with _plan(N, D, tau, 2, dtype, flin=kappa, fcub=0.0) as pl:
+            d = _to_dev(U0, dtype)
+            pl.run(d, n)
+            got = d.cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= TOL[dtype], (dtype, q, z, err)
