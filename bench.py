@@ -510,7 +510,7 @@ def main():
     ap.add_argument("--workload", default=inputs.AC2D_1024.name,
                     choices=sorted(inputs.WORKLOADS) + sorted(inputs.BATCH_WORKLOADS) + sorted(inputs.SNO_WORKLOADS))
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--route", default="auto", choices=["auto", "fft", "fft_half", "gemm_tf32", "gemm_bf16x3"])
+    ap.add_argument("--route", default="auto", choices=["auto", "fft", "fft_half", "fft_split", "gemm_tf32", "gemm_bf16x3"])
     ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time-step count")
     ap.add_argument("--ref-sample-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -64,6 +64,15 @@ typedef enum { ETD_F64 = 0, ETD_F32 = 1 } etd_dtype;            /* arithmetic an
  *   work; rounding grows like sqrt(N/2) eps).
  * ETD_ROUTE_AUTO: per axis, FP32 takes ETD_ROUTE_FFT for N >= 512 and ETD_ROUTE_FFT_HALF below;
  *   FP64 always takes the recurrence.
+ * ETD_ROUTE_FFT_SPLIT (FP32; otherwise as ETD_ROUTE_AUTO): Dirichlet axes of N = 1024 (strided ones when
+ *   N[0] is a multiple of 4) run a split-radix DST-I: the odd outputs are a DST-III of length N/2, the
+ *   even ones split once more into a DST-III of length N/4 and a DST-I of length N/4, each computed by a
+ *   complex FFT that fits in one warp (512, 256 and 512 points per pair of pencils against 2048 for the
+ *   odd extension; rounding grows like log N, and is smaller than the odd extension's in practice).
+ *   Exact arithmetic equal to the other FFT routes; batches take it as ETD_ROUTE_AUTO.
+ * FP32 2D plans on the FFT routes take the phi-function weights of the stage combinations from per-mode
+ * tables of FP64 values rounded once to FP32 (12 bytes per unknown for EIFE2, 4 for EIFE1, up to 64 MiB;
+ * larger and 3D plans evaluate them per mode in FP32).
  * ETD_ROUTE_GEMM_TF32 and ETD_ROUTE_GEMM_BF16X3 (FP32 plans only; every N[a] a multiple of 32):
  *   the DST-I along an axis is the dense product with the N x N sine matrix S_a of Section 4 (periodic
  *   plans: the N x N orthonormal Hartley matrix),
@@ -78,7 +87,8 @@ typedef enum {
   ETD_ROUTE_FFT = 1,
   ETD_ROUTE_FFT_HALF = 2,
   ETD_ROUTE_GEMM_TF32 = 3,
-  ETD_ROUTE_GEMM_BF16X3 = 4
+  ETD_ROUTE_GEMM_BF16X3 = 4,
+  ETD_ROUTE_FFT_SPLIT = 5
 } etd_route;
 
 typedef struct {

@@ -20,7 +20,7 @@ c_int, c_double, c_int64, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, c
 ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD_ERR_NONFINITE, ETD_ERR_TIMEOUT = range(7)
 ETD_DEBUG_STALL_FIRST_GEMM_PASS = 0x5A11
 ETD_F64, ETD_F32 = 0, 1
-ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3 = 0, 1, 2, 3, 4
+ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3, ETD_ROUTE_FFT_SPLIT = 0, 1, 2, 3, 4, 5
 ETD_BC_DIRICHLET, ETD_BC_PERIODIC = 0, 1
 ETD_NUM_PASS_KINDS = 9
 

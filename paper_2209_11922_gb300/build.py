@@ -82,6 +82,7 @@ def generate() -> list:
     srcs.append(os.path.join(CSRC, "etd_api.cu"))
     srcs.append(os.path.join(CSRC, "monitor_noalloc.cu"))
     srcs.append(os.path.join(CSRC, "gemm_inst.cu"))
+    srcs.append(os.path.join(CSRC, "split_inst.cu"))
     srcs.append(os.path.join(CSRC, "sno.cu"))
     return srcs
 

@@ -34,12 +34,15 @@
 #include "gemm_pass.cuh"
 #include "monitor.cuh"
 #include "pass_kernel.cuh"
+#include "split_pass.cuh"
 
 namespace etd {
 // registry of instantiated pass kernels (generated per (type, N) translation units)
 const KernelInfo* find_pass_kernel(int elem, int N, int variant);
 // tensor-core transform passes (gemm_inst.cu)
 const GemmKernelInfo* find_gemm_kernel(int bn, int route);
+// split-radix FP32 passes for axes of length 1024 (split_inst.cu), one kernel per PassOp
+const void* find_split_kernel(int op);
 }  // namespace etd
 
 using namespace etd;
@@ -112,6 +115,7 @@ struct etd_plan_s {
   etd_options opt{};
   int elem = 8;
   int odd[3] = {0, 0, 0};  // transform variant per axis: V_ODD, V_REC (DST-I) or V_HART (periodic)
+  int split[3] = {0, 0, 0};  // FP32 axes of length 1024 on the split-radix kernels (split_pass.cuh)
   int periodic = 0;        // every axis periodic (Hartley kernels), else homogeneous Dirichlet
   int nx = 1, ny = 1, nz = 1;
   size_t nfield = 0;       // pitched elements per field
@@ -122,6 +126,9 @@ struct etd_plan_s {
   void* F[5] = {};         // V, N0, V2, P, N2
   void* tables = nullptr;
   const void* tw[3] = {};
+  const void* stw[3] = {};   // twiddle tables of the split-radix kernels (split axes)
+  float* coef = nullptr;     // per-mode stage coefficients of the split last-axis passes (2D FP32)
+  size_t coef_s1 = 0, coef_s2 = 0, coef_rk1 = 0;   // float offsets of the S1, S2, RK1 tables
   const void* sn[3] = {};
   const void* zeta[3] = {};
   const void* ex[3] = {};
@@ -179,9 +186,70 @@ void fill_common(const etd_plan_s* pl, PassArgs<T>& a) {
 }
 
 // Build one pass launch. fields are indices into F (or -1 for a user pointer given later).
+// One pass of a split-radix axis (FP32, N = 1024): tiles of P = 2 pencil pairs (4 rows, 5 warps) along x
+// and of P = 4 pairs (8 columns: one 32-byte sector per row; 10 warps per transformed field) along strided
+// axes where the x extent allows, else 2.
+etd_status make_split_launch(etd_plan_s* pl, int op, int axis, const void* in0, const void* in1, void* out0,
+                             void* out1, int kind, double fields_rw, Launch& L) {
+  const void* fn = find_split_kernel(op);
+  if (!fn) return fail(ETD_ERR_UNSUPPORTED, "no split-radix kernel for pass %d", op);
+  PassArgs<float> a;
+  fill_common<float>(pl, a);
+  a.op = op;
+  a.axis = axis;
+  a.in0 = static_cast<const float*>(in0);
+  a.in1 = static_cast<const float*>(in1);
+  a.out0 = static_cast<float*>(out0);
+  a.out1 = static_cast<float*>(out1);
+  a.tw = static_cast<const float*>(pl->stw[axis]);
+  a.sn = nullptr;
+  a.sc = (float)pl->sc[axis];
+  a.lp = SPLIT_LPS;
+  int P = 2;
+  long long grid = 0;
+  if (axis == 0) {
+    a.npairs = pl->ny * pl->nz / 2;
+    grid = (a.npairs + P - 1) / P;
+  } else {
+    P = pl->nx % 8 == 0 ? 4 : 2;
+    if (pl->nx % (2 * P) != 0) return fail(ETD_ERR_UNSUPPORTED, "x extent %d is not a multiple of 4", pl->nx);
+    a.tiles_x = pl->nx / (2 * P);
+    grid = (long long)a.tiles_x * ((axis == 1) ? pl->nz : pl->ny);
+  }
+  a.P = P;
+  if (pl->coef) {
+    if (op == OP_S1) a.coef = pl->coef + pl->coef_s1;
+    else if (op == OP_S2) a.coef = pl->coef + pl->coef_s2;
+    else if (op == OP_RK1) a.coef = pl->coef + pl->coef_rk1;
+  }
+  const int nf = (op == OP_S1 || op == OP_RK1) ? 2 : 1;
+  L.fn = fn;
+  L.grid = dim3((unsigned)grid);
+  L.block = dim3((unsigned)(nf * (P / 2) * 160));
+  L.smem = split_smem_bytes(op, P);
+  L.kind = kind;
+  memcpy(L.args, &a, sizeof(a));
+  L.args_size = sizeof(a);
+  L.alg_bytes = fields_rw * (double)pl->unknowns * sizeof(float);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+  if (L.smem > (size_t)optin) return fail(ETD_ERR_UNSUPPORTED, "tile needs %zu B of shared memory (max %d)", L.smem, optin);
+  if (L.smem > 48 * 1024) {   // the device maximum: one kernel serves launches with different tile sizes
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "cudaFuncSetAttribute(%d B): %s", optin, cudaGetErrorString(e));
+  }
+  return ETD_OK;
+}
+
 template <class T>
 etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const void* in1, void* out0,
                        void* out1, int kind, double fields_rw, Launch& L) {
+  if constexpr (sizeof(T) == 4) {
+    // split-radix kernels, except under a time-dependent source or boundary data (whose passes add
+    // to the reaction field with the odd-extension kernels' epilogues)
+    if (pl->split[axis] && !pl->src_on && !pl->bnd_on && op != OP_PACK && op != OP_UNPACK)
+      return make_split_launch(pl, op, axis, in0, in1, out0, out1, kind, fields_rw, L);
+  }
   const int N = (int)pl->N[axis];
   const KernelInfo* k = find_pass_kernel((int)sizeof(T), N, pl->odd[axis]);
   if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", N);
@@ -196,6 +264,13 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   a.tw = static_cast<const T*>(pl->tw[axis]);
   a.sn = static_cast<const T*>(pl->sn[axis]);
   a.sc = (T)pl->sc[axis];
+  if constexpr (sizeof(T) == 4) {
+    if (pl->coef && pl->ndim == 2 && axis == 1) {
+      if (op == OP_S1) a.coef = pl->coef + pl->coef_s1;
+      else if (op == OP_S2) a.coef = pl->coef + pl->coef_s2;
+      else if (op == OP_RK1) a.coef = pl->coef + pl->coef_rk1;
+    }
+  }
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
   const int maxp = 512 / k->tpp > 0 ? 512 / k->tpp : 1;
   int P = 1;
@@ -782,14 +857,107 @@ void append_axis_tables(const KernelInfo* k, int n, double hh, double tauD, doub
   }
 }
 
+// Twiddle table of a split-radix axis (split_dst.cuh), FP64 values rounded once, appended at a 16-byte
+// boundary: the pre-twiddles (1/2) sqrt(2/N) e^{i pi k/N} (k < 512) and (1/2) sqrt(2/N) e^{i pi k/(N/2)}
+// (k < 256) of the two DST-III stages, and e^{2 pi i n k/512}, e^{2 pi i n k/256} for the twiddle step
+// of the 512- and 256-point FFTs.
+template <class T>
+size_t append_split_tables(std::vector<T>& h) {
+  while (h.size() % 4) h.push_back(T(0));
+  const size_t off = h.size();
+  const double n = (double)SPLIT_N, s = 0.5 * sqrt(2.0 / n);
+  auto put = [&](double ang, double scale) {
+    h.push_back((T)(scale * cos(ang)));
+    h.push_back((T)(scale * sin(ang)));
+  };
+  for (int k = 0; k < 512; ++k) put(M_PI * k / n, s);
+  for (int m = 1; m < 16; ++m)
+    for (int k = 0; k < 32; ++k) put(2.0 * M_PI * (double)(m * k) / 512.0, 1.0);
+  for (int k = 0; k < 256; ++k) put(M_PI * k / (0.5 * n), s);
+  for (int m = 1; m < 16; ++m)
+    for (int k = 0; k < 16; ++k) put(2.0 * M_PI * (double)(m * k) / 256.0, 1.0);
+  return off;
+}
+
+// phi_1(z), phi_2(z) in FP64 for z <= 0 (Section 2.2): the Taylor series sum_m z^m/(m+k)! for |z| < 1/2
+// (24 terms, truncation below 1e-20), the closed forms (e^z - 1)/z and (e^z - 1 - z)/z^2 through expm1
+// above, where their cancellation costs at most a few ulps.
+void phi12_fp64(double z, double& p1, double& p2) {
+  if (fabs(z) < 0.5) {
+    double s1 = 0, s2 = 0, t = 1, f1 = 1, f2 = 0.5;
+    for (int m = 0; m < 24; ++m) {
+      s1 += t * f1;
+      s2 += t * f2;
+      t *= z;
+      f1 /= (m + 2);
+      f2 /= (m + 3);
+    }
+    p1 = s1;
+    p2 = s2;
+  } else {
+    const double e = expm1(z);
+    p1 = e / z;
+    p2 = (e - z) / (z * z);
+  }
+}
+
+// Per-mode phi-function weights of a 2D FP32 plan whose y axis runs the split-radix kernels, computed in
+// FP64 from zeta = tau D (mu_x + mu_y) with the closed-form 1D rates (those of append_axis_tables) and
+// rounded once to FP32; layouts as documented for PassArgs::coef (the exponentials e^{-z}, e^{-c2 z} are
+// products of the per-axis tables).
+etd_status upload_coef_tables(etd_plan_s* pl) {
+  const int nx = pl->nx, ny = pl->ny;
+  const size_t modes = (size_t)nx * ny;
+  const double tauD = pl->tau * pl->D, c2 = pl->opt.c2, tau = pl->tau;
+  std::vector<double> mx(nx), my(ny);
+  auto mu = [](int i, int n, double hh) {
+    if (i == 0) return 0.0;
+    const double th = M_PI * (double)i / (double)n, s = sin(0.5 * th);
+    return 12.0 / (hh * hh) * s * s / (2.0 + cos(th));   // (6/h^2)(1 - cos)/(2 + cos)
+  };
+  for (int i = 0; i < nx; ++i) mx[i] = mu(i, nx, pl->h[0]);
+  for (int j = 0; j < ny; ++j) my[j] = mu(j, ny, pl->h[1]);
+  std::vector<float> h;
+  if (pl->scheme == 2) {
+    pl->coef_s1 = 0;
+    pl->coef_s2 = 2 * modes;
+    h.resize(3 * modes);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t m = (size_t)j * nx + i;
+        const double z = tauD * (mx[i] + my[j]);
+        double p1, p2, p1c, p2c;
+        phi12_fp64(-z, p1, p2);
+        phi12_fp64(-c2 * z, p1c, p2c);
+        h[2 * m + 0] = (float)(c2 * tau * p1c);
+        h[2 * m + 1] = (float)(tau * (p1 - p2 / c2));
+        h[2 * modes + m] = (float)(tau * p2 / c2);
+      }
+  } else {
+    pl->coef_rk1 = 0;
+    h.resize(modes);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t m = (size_t)j * nx + i;
+        double p1, p2;
+        phi12_fp64(-tauD * (mx[i] + my[j]), p1, p2);
+        h[m] = (float)(tau * p1);
+      }
+  }
+  ETD_CUDA(cudaMalloc(&pl->coef, h.size() * sizeof(float)));
+  ETD_CUDA(cudaMemcpy(pl->coef, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return ETD_OK;
+}
+
 template <class T>
 etd_status upload_tables(etd_plan_s* pl) {
   std::vector<T> h;
-  size_t offs[3][5];
+  size_t offs[3][5], soff[3] = {0, 0, 0};
   for (int a = 0; a < pl->ndim; ++a) {
     const KernelInfo* k = find_pass_kernel((int)sizeof(T), (int)pl->N[a], pl->odd[a]);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %lld", (long long)pl->N[a]);
     append_axis_tables<T>(k, (int)pl->N[a], pl->h[a], pl->tau * pl->D, pl->opt.c2, h, offs[a], pl->periodic != 0);
+    if (pl->split[a]) soff[a] = append_split_tables<T>(h);
     pl->sc[a] = pl->periodic ? 0.5 / sqrt((double)pl->N[a]) : 0.5 * sqrt(2.0 / (double)pl->N[a]);
   }
   ETD_CUDA(cudaMalloc(&pl->tables, h.size() * sizeof(T)));
@@ -801,6 +969,7 @@ etd_status upload_tables(etd_plan_s* pl) {
     pl->zeta[a] = base + offs[a][2];
     pl->ex[a] = base + offs[a][3];
     pl->ec[a] = base + offs[a][4];
+    pl->stw[a] = pl->split[a] ? base + soff[a] : nullptr;
   }
   for (int a = pl->ndim; a < 3; ++a) {   // unused third axis in 2D: point at axis 0 (never read)
     pl->tw[a] = pl->tw[0];
@@ -1246,7 +1415,7 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
     return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
   if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
   if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF &&
-      o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3)
+      o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3 && o.route != ETD_ROUTE_FFT_SPLIT)
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
   if (o.bc != ETD_BC_DIRICHLET && o.bc != ETD_BC_PERIODIC) return fail(ETD_ERR_INVALID_ARG, "unknown boundary condition");
   const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
@@ -1287,6 +1456,11 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
     else if (o.route == ETD_ROUTE_FFT) pl->odd[a] = V_ODD;
     else pl->odd[a] = N[a] >= 512 ? V_ODD : V_REC;
   }
+  // ETD_ROUTE_FFT_SPLIT: FP32 Dirichlet axes of length 1024 take the split-radix kernels (the strided
+  // passes need an x extent that is a multiple of 4); every other axis the AUTO choice.
+  for (int a = 0; a < ndim; ++a)
+    pl->split[a] = (o.dtype == ETD_F32 && !pl->periodic && o.route == ETD_ROUTE_FFT_SPLIT && N[a] == SPLIT_N &&
+                    (a == 0 || N[0] % 4 == 0)) ? 1 : 0;
   pl->nx = (int)N[0];
   pl->ny = (int)N[1];
   pl->nz = ndim == 3 ? (int)N[2] : 1;
@@ -1308,6 +1482,10 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   for (int f = 0; f < 5; ++f) pl->F[f] = static_cast<char*>(pl->ws) + f * fbytes;
   etd_status st = (pl->elem == 4) ? upload_tables<float>(pl) : upload_tables<double>(pl);
   if (st != ETD_OK) return bail(st);
+  // per-mode phi-function weights of the y passes of 2D FP32 plans on the FFT routes (at most 64 MiB)
+  if (ndim == 2 && pl->elem == 4 && !pl->periodic && !gemm && pl->nfield * (pl->scheme == 2 ? 12 : 4) <= ((size_t)64 << 20)) {
+    if ((st = upload_coef_tables(pl)) != ETD_OK) return bail(st);
+  }
   if (gemm) {
     pl->gemm = 1 + (o.route == ETD_ROUTE_GEMM_TF32 ? GR_TF32 : GR_BF16X3);
     if ((st = upload_gemm_tables(pl)) != ETD_OK) return bail(st);
@@ -1619,6 +1797,7 @@ etd_status etd_destroy(etd_plan pl) {
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   if (pl->ws) cudaFree(pl->ws);
   if (pl->tables) cudaFree(pl->tables);
+  if (pl->coef) cudaFree(pl->coef);
   if (pl->host_dev) cudaFree(pl->host_dev);
   if (pl->mon_part) cudaFree(pl->mon_part);
   if (pl->gtab) cudaFree(pl->gtab);
@@ -1649,7 +1828,7 @@ etd_status etd_batch_create(etd_batch* out, int count, const int64_t* N, const d
   if (!std::isfinite(o.flin) || !std::isfinite(o.fcub)) return fail(ETD_ERR_INVALID_ARG, "reaction coefficients must be finite");
   if (o.dtype != ETD_F32 && o.dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
   if (o.route != ETD_ROUTE_AUTO && o.route != ETD_ROUTE_FFT && o.route != ETD_ROUTE_FFT_HALF &&
-      o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3)
+      o.route != ETD_ROUTE_GEMM_TF32 && o.route != ETD_ROUTE_GEMM_BF16X3 && o.route != ETD_ROUTE_FFT_SPLIT)
     return fail(ETD_ERR_INVALID_ARG, "unknown route");
   const bool gemm = o.route == ETD_ROUTE_GEMM_TF32 || o.route == ETD_ROUTE_GEMM_BF16X3;
   if (gemm) return fail(ETD_ERR_UNSUPPORTED, "batches run the FFT routes only");

@@ -76,6 +76,10 @@ template <class T> struct PassArgs {
   const unsigned long long* step_ctr;    // time steps completed in the run
   unsigned long long* step_inc;          // the last pass of a step counts it (NULL: no)
   double src_amp, src_rate, src_c;
+  // Per-mode phi-function weights of the last-axis passes of FP32 2D plans (NULL: evaluated in the
+  // kernel), [y mode][x mode]: S1 float2 {c2 tau phi1(-c2 z), tau (phi1 - phi2/c2)(-z)}, S2 float
+  // tau phi2(-z)/c2, RK1 float tau phi1(-z).
+  const T* coef;
 };
 
 // Asynchronous global -> shared copies (cp.async): every load of a tile is in flight at once and
@@ -426,6 +430,56 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     return C{out[0], out[1]};
   };
 
+  // FP32 2D plans: the phi-function weights of the stage combination come from per-mode tables of FP64
+  // values rounded once (A.coef, [y mode][x mode]; e^{-z}, e^{-c2 z} are products of the per-axis
+  // factors), with every table load of a chunk of positions issued before the first use. Same
+  // effect on the buffers as the epilogue above.
+  // Compiled into the kernels with the full register budget only; the others evaluate the weights.
+  constexpr bool TABLES = sizeof(T) == 4 && pass_min_blocks<T, N>() == 1;
+  auto table_epilogue = [&](int kind, C* bpk) {
+    if constexpr (TABLES) {
+      constexpr int CNT = (N + TPP - 1) / TPP, CH = 4;
+      const size_t col = (size_t)x0 + 2 * p;
+#pragma unroll
+      for (int c0 = 0; c0 < CNT; c0 += CH) {
+        float4 cf4[CH];
+        float2 cf2[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int j = l + (c0 + c) * TPP;
+          if (c0 + c < CNT && j < N) {
+            const size_t m = ((size_t)j * A.nx + col) / 2;
+            if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(A.coef)[m];
+            else cf2[c] = reinterpret_cast<const float2*>(A.coef)[m];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int j = l + (c0 + c) * TPP;
+          if (c0 + c >= CNT || j >= N) continue;
+          const int aj = L::at(j);
+          const C w = bpk[aj];
+          if (kind == EPI_S1) {          // {c2 tau phi1(-c2 z), tau (phi1 - phi2/c2)(-z)} per mode
+            const C u = b0p[aj];
+            b0p[aj] = C{pc[0] * cj[j] * u.x + cf4[c].x * w.x, pc[1] * cj[j] * u.y + cf4[c].z * w.y};
+            bpk[aj] = C{pe[0] * ej[j] * u.x + cf4[c].y * w.x, pe[1] * ej[j] * u.y + cf4[c].w * w.y};
+          } else if (kind == EPI_RK1) {  // tau phi1(-z) per mode
+            const C u = b0p[aj];
+            b0p[aj] = C{pe[0] * ej[j] * u.x + cf2[c].x * w.x, pe[1] * ej[j] * u.y + cf2[c].y * w.y};
+          } else {                       // S2: tau phi2(-z)/c2 per mode; P in the second buffer
+            const C pp = b1p[aj];
+            bpk[aj] = C{pp.x + cf2[c].x * w.x, pp.y + cf2[c].y * w.y};
+          }
+        }
+      }
+      __syncthreads();
+    }
+  };
+  auto stage_epilogue = [&](int kind, C* bpk) {
+    if (TABLES && A.coef) table_epilogue(kind, bpk);
+    else epilogue_pair<T, N, VAR>(bpk, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
+  };
+
   // Odd-extension kernels with the full register budget (one CTA of 512 threads per SM) run the
   // two forward transforms of RK1/S1 (of U and of N0) together, sharing each Stockham pass's
   // barriers; under the halved budget the second set of butterfly registers would spill.
@@ -435,7 +489,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       C* const bps[2] = {b0p, b1p};
       C* const scrs[2] = {scrp, scrp};   // unused by the odd-extension variant
       dst_pairs<T, N, VAR, 2>(bps, tw, sn, l, scrs, A.sc);
-      epilogue_pair<T, N, VAR>(b1p, l, [&](int j, C w) -> C { return epilogue(epi[1], j, w); });
+      stage_epilogue(epi[1], b1p);
       if (op == OP_S1) store_tile(b1, A.out1);
       s0 = 2;
     }
@@ -458,7 +512,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     }
     const React<T> rx{op == OP_REACT && s == 1 && !logr, A.flin, A.fcub};
     dst_pair<T, N, VAR>(bp, tw, sn, l, scrp, A.sc, rx);
-    if (kind != EPI_PLAIN) epilogue_pair<T, N, VAR>(bp, l, [&](int j, C w) -> C { return epilogue(kind, j, w); });
+    if (kind != EPI_PLAIN) stage_epilogue(kind, bp);
     if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
   }
 

@@ -15,7 +15,8 @@ from . import _native as nat
 _DT = {"f64": nat.ETD_F64, "f32": nat.ETD_F32}
 _BC = {"dirichlet": nat.ETD_BC_DIRICHLET, "periodic": nat.ETD_BC_PERIODIC}
 _ROUTE = {"auto": nat.ETD_ROUTE_AUTO, "fft": nat.ETD_ROUTE_FFT, "fft_half": nat.ETD_ROUTE_FFT_HALF,
-          "gemm_tf32": nat.ETD_ROUTE_GEMM_TF32, "gemm_bf16x3": nat.ETD_ROUTE_GEMM_BF16X3}
+          "gemm_tf32": nat.ETD_ROUTE_GEMM_TF32, "gemm_bf16x3": nat.ETD_ROUTE_GEMM_BF16X3,
+          "fft_split": nat.ETD_ROUTE_FFT_SPLIT}
 
 
 def _torch():
