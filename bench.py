@@ -308,6 +308,17 @@ def run_gb300(args, w):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        if world == 1 and not args.no_extras and w is inputs.AC2D_1024:
+            # the other configurations of the workload set, measured after the headline (outside its
+            # timed region): 256^3 on every route, the split-radix route, the batch and the surrogate
+            line["route_fft_split_2d_1024"] = measure_split_route(args)
+            line["config3_3d_256cubed"] = measure_3d(args)
+            line["config4_batched"] = measure_batched(args, inputs.BATCH_2D_512, 3, 3)
+            sno = measure_sno(args, inputs.SNO_256)
+            line["config5_surrogate"] = {k: sno[k] for k in (
+                "metric", "value", "unit", "config", "plain_ms", "parareal_sno_ms", "parareal_sno", "final_rel_l2_sno",
+                "parareal_etdrk2_coarse_ms", "parareal_etdrk2_coarse", "final_rel_l2_etdrk2",
+                "gain_vs_nonlearned_coarse", "coarse_sno_ms", "roofline") if k in sno}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -315,15 +326,13 @@ def run_gb300(args, w):
     return 0
 
 
-def run_batched(args, bw):
+def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
     """Many independent 2D problems advanced by one batch (grouped launches), against the same
-    problems advanced one plan each (the plain GPU solver)."""
+    problems advanced one plan each (the plain GPU solver). Returns the measured figures."""
     import torch
 
     from paper_2209_11922_gb300.etd import Batch, Plan
 
-    world, rank, local = _dist_setup(args)
-    torch.cuda.set_device(local)
     probs = bw.problems()
     dtype = args.dtype
     npdt = np.float32 if dtype == "f32" else np.float64
@@ -337,7 +346,7 @@ def run_batched(args, bw):
     flat = torch.empty_like(flat0)
     fields = [flat[int(offs[i]):int(offs[i + 1])].view(shp) for i, shp in enumerate(shapes)]
     unknowns = int(offs[-1])
-    nsteps = args.time_steps or bw.nsteps
+    nsteps = nsteps or bw.nsteps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
@@ -358,10 +367,9 @@ def run_batched(args, bw):
             tot += e0.elapsed_time(e1)
         return tot
 
-    timed(lambda: batch.run(fields, nsteps, stream), args.warmup)
-    with ClockSampler(local) as clk:
-        ms = timed(lambda: batch.run(fields, nsteps, stream), args.steps)
-    value = unknowns * nsteps * args.steps / (ms * 1e-3)
+    timed(lambda: batch.run(fields, nsteps, stream), warmup)
+    ms = timed(lambda: batch.run(fields, nsteps, stream), steps)
+    value = unknowns * nsteps * steps / (ms * 1e-3)
     # plain GPU solver: one plan per problem, run one after the other on the same stream
     plans = [Plan(N, D, bw.tau, 2, dtype, route=args.route) for N, D in probs]
 
@@ -370,38 +378,53 @@ def run_batched(args, bw):
             pl.run(f, nsteps, stream)
 
     timed(run_plans, 1)
-    ms_plans = timed(run_plans, max(1, args.steps // 2))
-    value_plans = unknowns * nsteps * max(1, args.steps // 2) / (ms_plans * 1e-3)
+    psteps = max(1, steps // 2)
+    ms_plans = timed(run_plans, psteps)
+    value_plans = unknowns * nsteps * psteps / (ms_plans * 1e-3)
     for pl in plans:
         pl.close()
+    batch.close()
     esz = 4 if dtype == "f32" else 8
-    step_bytes = 11 * unknowns * esz
-    achieved = step_bytes / (ms / args.steps / nsteps * 1e-3) / 1e9
+    achieved = 11 * unknowns * esz / (ms / steps / nsteps * 1e-3) / 1e9
     peak, peak_src = _peaks()
+    return {"workload": bw.name, "problems": len(probs), "unknowns": unknowns, "time_steps_per_run": nsteps,
+            "value": value, "unit": UNIT, "ms_per_run": ms / steps, "plans_value": value_plans,
+            "speedup_vs_plans": value / value_plans, "launches_per_time_step": info["launches_per_step"],
+            "tuned_tile_pairs": info["tile_pairs"], "create_s": round(create_s, 3), "runs_timed": steps,
+            "gpu_launches": steps * (info["launches_per_step"] * nsteps + 12),
+            "roofline": {"bound": "hbm", "kernel": "one time step (all grouped launches)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": None}}
+
+
+def run_batched(args, bw):
+    """The batched workload as its own bench line."""
+    import torch
+
+    world, rank, local = _dist_setup(args)
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        m = measure_batched(args, bw, args.steps, args.warmup, args.time_steps)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": dtype, "data": "synthetic",
-        "config": {"workload": bw.name, "problems": len(probs), "unknowns": unknowns, "time_steps_per_step": nsteps,
-                   "tau": bw.tau, "scheme": "ETDRK2", "launches_per_time_step": info["launches_per_step"],
-                   "tuned_tile_pairs": info["tile_pairs"], "create_s": round(create_s, 3),
-                   "l2": "256 MiB buffer written between bench steps"},
-        "gpu_launches": args.steps * (info["launches_per_step"] * nsteps + 12),
-        "plans_value": value_plans, "speedup_vs_plans": value / value_plans,
-        "roofline": {"bound": "hbm", "kernel": "one time step (all grouped launches)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None},
-        "clocks": clk.summary(),
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_run"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": bw.name, "problems": m["problems"], "unknowns": m["unknowns"],
+                   "time_steps_per_step": m["time_steps_per_run"], "tau": bw.tau, "scheme": "ETDRK2",
+                   "launches_per_time_step": m["launches_per_time_step"], "tuned_tile_pairs": m["tuned_tile_pairs"],
+                   "create_s": m["create_s"], "l2": "256 MiB buffer written between bench steps"},
+        "gpu_launches": m["gpu_launches"], "plans_value": m["plans_value"],
+        "speedup_vs_plans": m["speedup_vs_plans"], "roofline": m["roofline"], "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
-    batch.close()
     return 0
 
 
-def run_sno_parareal(args, sw):
+def measure_sno(args, sw) -> dict:
     """Parareal with the trained SNO as coarse propagator against the plain batched ETDRK2 solver on
     B problems at N x N (windows x window steps). Training (data from the plain solver, Adam) runs
     before the timed region. Also times Parareal with a non-learned coarse propagator (one ETDRK2
-    step of window * tau) to show what the learning gains."""
+    step of window * tau) to show what the learning gains. Returns the bench line as a dict."""
     import torch
 
     from paper_2209_11922_gb300.etd import Batch
@@ -495,10 +518,100 @@ def run_sno_parareal(args, sw):
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "traffic": None},
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
     for o in (pr_sno, pr_big, sno, plain):
         o.close()
+    return line
+
+
+def run_sno_parareal(args, sw):
+    print(json.dumps(measure_sno(args, sw)), flush=True)
     return 0
+
+
+def measure_3d(args) -> dict:
+    """The 256^3 Allen-Cahn workload (255^3 unknowns, D = 1e-3, tau = 1e-2, ETDRK2, FP32) on each
+    transform route: time per ETDRK2 step (events around a run of time steps after warm-up runs; the
+    330 MB of fields exceed L2), unknown-updates/s, the step-level fraction of HBM bandwidth on the
+    pass schedule's field passes (FFT routes 19 per step, GEMM routes 27, 4 bytes each), and the route's
+    error against the oracle on the same configuration at 64^3 (63^3 unknowns, 5 steps)."""
+    import torch
+
+    from oracle import etd as oetd
+    from paper_2209_11922_gb300.etd import Plan
+
+    w, ws = inputs.AC3D_256, inputs.AC3D_64
+    peak, peak_src = _peaks()
+    nsteps = 20
+    u0 = torch.from_numpy(w.u0().astype(np.float32)).cuda()
+    U0s = ws.u0().astype(np.float32).astype(np.float64)
+    ref = oetd.run(U0s, ws.N, ws.h, ws.D, ws.tau, 5, 2)
+    out = {"workload": w.name, "unknowns": w.unknowns, "time_steps_timed": nsteps,
+           "error_case": f"{ws.name}, 5 steps, rel L2 / rel Linf against the FP64 oracle", "routes": {}}
+    stream = torch.cuda.current_stream()
+    for route, passes in (("auto", 19), ("gemm_tf32", 27), ("gemm_bf16x3", 27)):
+        with Plan(w.N, w.D, w.tau, 2, "f32", route=route) as pl:
+            u = torch.empty_like(u0)
+            for _ in range(2):
+                u.copy_(u0)
+                pl.run(u, nsteps, stream)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(3):
+                u.copy_(u0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.run(u, nsteps, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / nsteps)
+            prof = pl.run_profiled(u, 4, stream)
+        ms = min(ts)
+        with Plan(ws.N, ws.D, ws.tau, 2, "f32", route=route) as pl:
+            d = torch.from_numpy(U0s.astype(np.float32)).cuda()
+            pl.run(d, 5)
+            got = d.cpu().numpy().astype(np.float64)
+        achieved = passes * 4 * w.unknowns / (ms * 1e-3) / 1e9
+        out["routes"][route] = {
+            "ms_per_time_step": ms, "value": w.unknowns / (ms * 1e-3), "unit": UNIT,
+            "field_passes_per_step": passes, "achieved_GBps": achieved, "peak": peak, "peak_source": peak_src,
+            "frac": achieved / peak,
+            "pass_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in prof.items() if v[1] > 0},
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "rel_linf": float(np.abs(got - ref).max() / np.abs(ref).max())}
+    return out
+
+
+def measure_split_route(args) -> dict:
+    """The headline workload on the split-radix FFT route against the default route: time per ETDRK2
+    step over a 2000-step run and the error of 100 steps against the FP64 oracle, both routes."""
+    import torch
+
+    from oracle import etd as oetd
+    from paper_2209_11922_gb300.etd import Plan
+
+    w = inputs.AC2D_1024
+    U0 = w.u0().astype(np.float32)
+    ref = oetd.run(U0.astype(np.float64), w.N, w.h, w.D, w.tau, 100, 2)
+    stream = torch.cuda.current_stream()
+    out = {"workload": w.name, "error_case": "100 ETDRK2 steps, rel L2 / rel Linf against the FP64 oracle"}
+    for route in ("auto", "fft_split"):
+        with Plan(w.N, w.D, w.tau, 2, "f32", route=route) as pl:
+            u = torch.from_numpy(U0).cuda()
+            pl.run(u, 100)
+            got = u.cpu().numpy().astype(np.float64)
+            for _ in range(2):
+                u.copy_(torch.from_numpy(U0))
+                pl.run(u, 200, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pl.run(u, 2000, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out[route] = {"ms_per_time_step": e0.elapsed_time(e1) / 2000,
+                      "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                      "rel_linf": float(np.abs(got - ref).max() / np.abs(ref).max())}
+    return out
 
 
 def main():
@@ -515,6 +628,8 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (256^3 routes, split route, batch, surrogate)")
     ap.add_argument("--sno-trajectories", type=int, default=0, help="training trajectories (default: the workload's)")
     ap.add_argument("--sno-epochs", type=int, default=6)
     ap.add_argument("--sno-lr", type=float, default=1e-3)

@@ -277,15 +277,12 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   long long grid = 0;
   if (axis == 0) {
     a.npairs = pl->ny * pl->nz / 2;
-    P = env_int("ETD_PAIRS_X", 0);
-    if (P <= 0) {
-      // CTAs of about 64 threads (at least one pencil pair): with many small CTAs per SM the
-      // barrier-separated phases of different CTAs interleave (255^3 FP32: P = 8 ran the x passes 13%
-      // faster than 512-thread CTAs; 128^3 periodic: 2%).
-      P = 64 / k->tpp > 1 ? 64 / k->tpp : 1;
-      if (P > maxp) P = maxp;
-      while (P > 1 && (a.npairs + P - 1) / P < 2 * pl->num_sms) P /= 2;
-    }
+    // CTAs of about 64 threads (at least one pencil pair): with many small CTAs per SM the
+    // barrier-separated phases of different CTAs interleave (255^3 FP32: P = 8 ran the x passes 13%
+    // faster than 512-thread CTAs; 128^3 periodic: 2%).
+    P = 64 / k->tpp > 1 ? 64 / k->tpp : 1;
+    if (P > maxp) P = maxp;
+    while (P > 1 && (a.npairs + P - 1) / P < 2 * pl->num_sms) P /= 2;
     if (P > maxp) P = maxp;
     grid = (a.npairs + P - 1) / P;
   } else {
@@ -295,11 +292,8 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
     // than P = 2 with 256 CTAs, and P = 1 was 40% slower).
     const int pmin = 16 / (int)sizeof(T);
     const int pmax = 64 / (int)sizeof(T);   // 128-byte row segments: wider tiles gained nothing
-    P = env_int("ETD_PAIRS_STRIDED", 0);
-    if (P <= 0) {
-      P = maxp < pmax ? maxp : pmax;
-      while (P > pmin && (pl->nx / (2 * P)) * (long long)other < 2 * pl->num_sms) P /= 2;
-    }
+    P = maxp < pmax ? maxp : pmax;
+    while (P > pmin && (pl->nx / (2 * P)) * (long long)other < 2 * pl->num_sms) P /= 2;
     if (P > maxp) P = maxp;
     while (P > 1 && pl->nx % (2 * P) != 0) P /= 2;
     if (pl->nx % (2 * P) != 0) return fail(ETD_ERR_UNSUPPORTED, "x extent %d not even", pl->nx);
