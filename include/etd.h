@@ -239,6 +239,18 @@ typedef struct {
 /* Describe a plan. */
 etd_status etd_get_plan_info(etd_plan plan, etd_plan_info* info);
 
+/* The phi-function weights of the stage combinations (eqs. (2.13)/(2.14); phi_k of Section 2.2) as the
+ * FFT pass kernels evaluate them per mode, in the arithmetic of dtype: for each of the n modes, from
+ * zeta[i] = tau lambda_i >= 0, E[i] = e^{-zeta} and Ec[i] = e^{-c2 zeta} (HOST arrays, rounded to dtype
+ * on the device as the kernels' tables hold them), writes out[3i] = phi_1(-zeta), out[3i+1] =
+ * phi_2(-zeta), out[3i+2] = c2 phi_1(-c2 zeta) (HOST array of 3n doubles). These are the weights of 3D
+ * plans and of 2D plans above the per-mode table size; 2D FP32 plans otherwise use FP64 values rounded
+ * once. For checking their accuracy; allocates a temporary device buffer and synchronises. Errors:
+ * ETD_ERR_INVALID_ARG for NULL arrays (n > 0), n < 0, c2 outside (0, 1], negative or non-finite zeta,
+ * non-finite E or Ec. */
+etd_status etd_phi_weights(etd_dtype dtype, int64_t n, const double* zeta, const double* E, const double* Ec,
+                           double c2, double* out);
+
 /* Name of pass kind k (0 <= k < ETD_NUM_PASS_KINDS), or NULL. */
 const char* etd_pass_kind_name(int k);
 

@@ -72,6 +72,8 @@ _SIGS = {
     "etd_batch_destroy": (c_int, [c_void_p]),
     "etd_monitor_noalloc": (c_int, [c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), c_double, c_int,
                                     c_void_p, c_void_p, c_void_p]),
+    "etd_phi_weights": (c_int, [c_int, c_int64, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                ctypes.POINTER(c_double), c_double, ctypes.POINTER(c_double)]),
     "etd_sno_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int]),
     "etd_sno_param_count": (c_int64, [c_void_p]),
     "etd_sno_set_params": (c_int, [c_void_p, c_void_p]),

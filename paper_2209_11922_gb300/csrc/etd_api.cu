@@ -1376,7 +1376,56 @@ etd_status batch_run_steps(etd_batch_s* b, int64_t nsteps, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+// One mode per thread: the weights as the pass epilogues evaluate them, from inputs rounded to T.
+template <class T>
+__global__ void phi_weights_kernel(const double* __restrict__ zeta, const double* __restrict__ E,
+                                   const double* __restrict__ Ec, double c2, long long n, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned act = __activemask();
+  const T z = (T)zeta[i];
+  T p1, p2, rz;
+  stage_phi12<T>(z, (T)E[i], act, p1, p2, rz);
+  const T p1c = stage_phi1c<T>(z, (T)Ec[i], (T)c2, rz, act);
+  out[3 * i] = (double)p1;
+  out[3 * i + 1] = (double)p2;
+  out[3 * i + 2] = (double)p1c;
+}
+}  // namespace
+
 extern "C" {
+
+etd_status etd_phi_weights(etd_dtype dtype, int64_t n, const double* zeta, const double* E, const double* Ec,
+                           double c2, double* out) {
+  g_last_error.clear();
+  if (dtype != ETD_F32 && dtype != ETD_F64) return fail(ETD_ERR_INVALID_ARG, "dtype must be ETD_F32 or ETD_F64");
+  if (n < 0) return fail(ETD_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && (!zeta || !E || !Ec || !out)) return fail(ETD_ERR_INVALID_ARG, "NULL array");
+  if (!(std::isfinite(c2) && c2 > 0 && c2 <= 1)) return fail(ETD_ERR_INVALID_ARG, "c2 must lie in (0, 1]");
+  for (int64_t i = 0; i < n; ++i)
+    if (!(std::isfinite(zeta[i]) && zeta[i] >= 0) || !std::isfinite(E[i]) || !std::isfinite(Ec[i]))
+      return fail(ETD_ERR_INVALID_ARG, "zeta must be finite and >= 0, E and Ec finite (entry %lld)", (long long)i);
+  if (n == 0) return ETD_OK;
+  double* d = nullptr;
+  const size_t in_bytes = 3 * (size_t)n * sizeof(double);
+  cudaError_t e = cudaMalloc(&d, 2 * in_bytes);
+  if (e != cudaSuccess) return fail(ETD_ERR_OOM, "device buffer: %s", cudaGetErrorString(e));
+  etd_status st = ETD_OK;
+  if ((e = cudaMemcpy(d, zeta, n * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d + n, E, n * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d + 2 * n, Ec, n * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    st = fail(ETD_ERR_CUDA, "copy in: %s", cudaGetErrorString(e));
+  } else {
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (dtype == ETD_F32) phi_weights_kernel<float><<<blocks, 256>>>(d, d + n, d + 2 * n, c2, n, d + 3 * n);
+    else phi_weights_kernel<double><<<blocks, 256>>>(d, d + n, d + 2 * n, c2, n, d + 3 * n);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaMemcpy(out, d + 3 * n, in_bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      st = fail(ETD_ERR_CUDA, "phi weights: %s", cudaGetErrorString(e));
+  }
+  cudaFree(d);
+  return st;
+}
 
 etd_status etd_options_default(etd_options* opt) {
   if (!opt) return fail(ETD_ERR_INVALID_ARG, "opt is NULL");

@@ -71,6 +71,37 @@ template <class T> __device__ __forceinline__ T phi1_sel(T zeta, T E) {
   return small ? T(1) - zeta * s2 : (T(1) - E) * rz;
 }
 
+// The phi-function weights of one mode as the FFT pass epilogues evaluate them in type T (the
+// per-mode path: 3D plans, and 2D plans without per-mode weight tables), from zeta = tau lambda >= 0 and
+// E = e^{-zeta} as stored (products of per-axis factors): phi_1(-zeta), phi_2(-zeta) by the closed forms
+// with one correctly rounded reciprocal rz = 1/zeta for zeta >= 1, and below by the series of phi_2 with
+// phi_1 = 1 - zeta phi_2; the series runs only in warps holding such a mode (act: the calling lanes,
+// every one of which votes with its own predicate).
+template <class T>
+__device__ __forceinline__ void stage_phi12(T zeta, T E, unsigned act, T& p1, T& p2, T& rz) {
+  const bool small = zeta < T(1);
+  rz = rcp_rn(small ? T(1) : zeta);
+  p1 = (T(1) - E) * rz;
+  p2 = (T(1) - p1) * rz;
+  if (__any_sync(act, small)) {
+    const T s2 = phi2_series<T>(small ? -zeta : T(0));
+    p2 = small ? s2 : p2;
+    p1 = small ? T(1) - zeta * s2 : p1;
+  }
+}
+// c2 phi_1(-c2 zeta) with Ec = e^{-c2 zeta}: (1 - Ec) / zeta from rz for c2 zeta >= 1, the series below.
+template <class T>
+__device__ __forceinline__ T stage_phi1c(T zeta, T Ec, T c2, T rz, unsigned act) {
+  const T zc = c2 * zeta;
+  T t = (T(1) - Ec) * rz;
+  const bool smc = zc < T(1);
+  if (__any_sync(act, smc)) {
+    const T s2c = phi2_series<T>(smc ? -zc : T(0));
+    t = smc ? c2 * (T(1) - zc * s2c) : t;
+  }
+  return t;
+}
+
 // Programmatic dependent launch: wait until the previous kernel in the stream has completed and its
 // writes are visible (a no-op when launched without the attribute), and let the next kernel start
 // its prologue early. Every pass waits before its first read of a field.

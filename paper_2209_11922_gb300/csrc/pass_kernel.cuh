@@ -371,12 +371,8 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const T zeta = pz[t] + zjj, E = pe[t] * ejj;
-        const bool small = zeta < T(1);
-        T p1 = (T(1) - E) * rcp_rn(small ? T(1) : zeta);
-        if (__any_sync(act, small)) {
-          const T s2 = phi2_series<T>(small ? -zeta : T(0));
-          p1 = small ? T(1) - zeta * s2 : p1;
-        }
+        T p1, p2, rz;
+        stage_phi12<T>(zeta, E, act, p1, p2, rz);
         out[t] = E * uv[t] + tau * p1 * wv[t];
       }
       b0p[L::at(j)] = C{out[0], out[1]};
@@ -389,23 +385,10 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       T u2[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj, zc = c2 * zeta;
-        const bool small = zeta < T(1);
-        const T rz = rcp_rn(small ? T(1) : zeta);
-        T p1 = (T(1) - E) * rz;
-        T p2 = (T(1) - p1) * rz;
-        if (__any_sync(act, small)) {
-          const T s2 = phi2_series<T>(small ? -zeta : T(0));
-          p2 = small ? s2 : p2;
-          p1 = small ? T(1) - zeta * s2 : p1;
-        }
-        // c2 tau phi1(-c2 zeta) = tau (1 - Ec) / zeta for c2 zeta >= 1
-        T t1 = tau * (T(1) - Ec) * rz;
-        const bool smc = zc < T(1);
-        if (__any_sync(act, smc)) {
-          const T s2c = phi2_series<T>(smc ? -zc : T(0));
-          t1 = smc ? c2 * tau * (T(1) - zc * s2c) : t1;
-        }
+        const T zeta = pz[t] + zjj, E = pe[t] * ejj, Ec = pc[t] * cjj;
+        T p1, p2, rz;
+        stage_phi12<T>(zeta, E, act, p1, p2, rz);
+        const T t1 = tau * stage_phi1c<T>(zeta, Ec, c2, rz, act);   // c2 tau phi1(-c2 zeta)
         u2[t] = Ec * uv[t] + t1 * wv[t];
         out[t] = E * uv[t] + tau * (p1 - p2 * inv_c2) * wv[t];
       }
@@ -418,13 +401,8 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const T zeta = pz[t] + zjj, E = pe[t] * ejj;
-      const bool small = zeta < T(1);
-      const T rz = rcp_rn(small ? T(1) : zeta);
-      T p2 = (T(1) - (T(1) - E) * rz) * rz;
-      if (__any_sync(act, small)) {
-        const T s2 = phi2_series<T>(small ? -zeta : T(0));
-        p2 = small ? s2 : p2;
-      }
+      T p1, p2, rz;
+      stage_phi12<T>(zeta, E, act, p1, p2, rz);
       out[t] = pv[t] + (tau * inv_c2) * p2 * wv[t];
     }
     return C{out[0], out[1]};

@@ -105,38 +105,16 @@ __device__ __forceinline__ void split_epilogue(const PassArgs<float>& A, int P, 
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const float zeta = qz[2 * p + s] + tz[j], E = qe[2 * p + s] * te[j];
-      const bool small = zeta < 1.f;
-      const float rz = rcp_rn(small ? 1.f : zeta);
+      float p1, p2, rz;
+      stage_phi12<float>(zeta, E, act, p1, p2, rz);
       if constexpr (OP == OP_RK1) {
-        float p1 = (1.f - E) * rz;
-        if (__any_sync(act, small)) {
-          const float s2 = phi2_series<float>(small ? -zeta : 0.f);
-          p1 = small ? 1.f - zeta * s2 : p1;
-        }
         o0[s] = E * uv[s] + tau * p1 * wv[s];
       } else if constexpr (OP == OP_S1) {
-        const float Ec = qc[2 * p + s] * tc[j], zc = c2 * zeta;
-        float p1 = (1.f - E) * rz;
-        float p2 = (1.f - p1) * rz;
-        if (__any_sync(act, small)) {
-          const float s2 = phi2_series<float>(small ? -zeta : 0.f);
-          p2 = small ? s2 : p2;
-          p1 = small ? 1.f - zeta * s2 : p1;
-        }
-        float t1 = tau * (1.f - Ec) * rz;   // c2 tau phi1(-c2 zeta) for c2 zeta >= 1
-        const bool smc = zc < 1.f;
-        if (__any_sync(act, smc)) {
-          const float s2c = phi2_series<float>(smc ? -zc : 0.f);
-          t1 = smc ? c2 * tau * (1.f - zc * s2c) : t1;
-        }
+        const float Ec = qc[2 * p + s] * tc[j];
+        const float t1 = tau * stage_phi1c<float>(zeta, Ec, c2, rz, act);   // c2 tau phi1(-c2 zeta)
         o0[s] = Ec * uv[s] + t1 * wv[s];                          // U2~
         o1[s] = E * uv[s] + tau * (p1 - p2 * inv_c2) * wv[s];      // P
       } else {   // S2: b0 = N2~, b1 = P
-        float p2 = (1.f - (1.f - E) * rz) * rz;
-        if (__any_sync(act, small)) {
-          const float s2 = phi2_series<float>(small ? -zeta : 0.f);
-          p2 = small ? s2 : p2;
-        }
         o0[s] = wv[s] + (tau * inv_c2) * p2 * uv[s];
       }
     }

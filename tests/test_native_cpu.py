@@ -233,3 +233,15 @@ def test_noalloc_monitor_rejects_oversize_without_overflow(L, N):
     dummy = ctypes.c_void_p(256)   # never dereferenced: the call fails in its argument checks
     st = L.etd_monitor_noalloc(3, Na, ha, 0.1, nat.ETD_F32, dummy, dummy, None)
     assert st == nat.ETD_ERR_INVALID_ARG and b"maximum" in L.etd_last_error()
+
+
+def test_phi_weights_arguments_rejected_on_the_host(L):
+    arr = (ctypes.c_double * 3)(0.1, 1.0, 2.0)
+    out = (ctypes.c_double * 9)()
+    assert L.etd_phi_weights(7, 3, arr, arr, arr, 0.5, out) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_phi_weights(nat.ETD_F32, -1, arr, arr, arr, 0.5, out) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_phi_weights(nat.ETD_F32, 3, None, arr, arr, 0.5, out) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_phi_weights(nat.ETD_F32, 3, arr, arr, arr, 1.5, out) == nat.ETD_ERR_INVALID_ARG
+    bad = (ctypes.c_double * 3)(0.1, -1.0, 2.0)
+    assert L.etd_phi_weights(nat.ETD_F64, 3, bad, arr, arr, 0.5, out) == nat.ETD_ERR_INVALID_ARG
+    assert L.etd_phi_weights(nat.ETD_F64, 0, None, None, None, 0.5, None) == nat.ETD_OK
