@@ -72,14 +72,17 @@ etd_status etd_parareal_create(etd_parareal* out, etd_sno sno, int N, int B, con
 typedef struct {
   int iterations;          /* Parareal iterations run (fine sweeps) */
   int fallbacks;           /* windows advanced by the plain solver after a rejected correction */
-  double correction[32];   /* max over problems of the last-window correction rel L2 per iteration */
+  double correction[32];   /* per iteration: max over problems and updated windows of the correction rel L2 */
 } etd_parareal_stats;
 
 /* Run from u0 (device, B fields) and write the final state to u_out (device). Iterates until the
- * largest per-window correction (rel L2, max over problems) falls below tol or `max_iter` fine sweeps
- * ran. A window whose correction exceeds fallback_tol in an iteration after the first is recomputed
- * by the fine solver from its corrected start (counted in stats->fallbacks), so later windows start
- * from plain-solver states. Synchronises. */
+ * largest per-window correction (rel L2, max over problems) falls below tol, every window is converged,
+ * or `max_iter` fine sweeps ran. Windows whose start is already the fine solution (u0, then one more
+ * window per iteration, and windows advanced by the fine solver from such a start) take F of that start
+ * and keep it: the update's value in exact arithmetic, without the coarse propagator's rounding. A
+ * window whose correction exceeds fallback_tol in an iteration after the first is recomputed by the
+ * fine solver from its corrected start (counted in stats->fallbacks), so later windows start from
+ * plain-solver states. Synchronises. */
 etd_status etd_parareal_run(etd_parareal p, const float* u0, float* u_out, int max_iter, double tol,
                             double fallback_tol, etd_parareal_stats* stats, void* stream);
 

@@ -10,15 +10,17 @@ axis, S_M[p][j] = sqrt(2/N) sin((p+1)(j+1) pi / N), p < M, j < N-1:
     a      = (ln D - ln 1e-3) / ln 100                         (input feature, ~[-1/2, 1/2])
     h_0[c] = Wl[c,0] u + Wl[c,1] a + bl[c]                      (lift, c < C)
     layer l = 0..L-1:
-      hh[c]    = S_M h_l[c] S_M^T                               (M x M modes)
+      hh[c]    = S_M (bf(h_l[c]) bf(S_M)^T)                     (M x M modes; the inner product bf16)
       gh[o]    = sum_c bf(Wm[l,p,q,o,c]) bf(hh[c,p,q])          (per-mode channel mix, bf16 operands)
-      z_l[o]   = S_M^T gh[o] S_M + sum_c Wp[l,o,c] h_l[c] + bp[l,o]
+      z_l[o]   = bf(S_M)^T bf(gh[o] S_M) + sum_c bf(Wp[l,o,c]) bf(h_l[c]) + bp[l,o]
       h_{l+1}  = gelu(z_l),  gelu(z) = z/2 (1 + erf(z / sqrt 2))
     u_hat  = u + sum_c Wq[c] h_L[c] + bq                        (projection onto the increment)
 
 bf(x) rounds to bfloat16 (round to nearest, ties to even) after rounding to float32, the precision
-the CUDA path rounds from. Loss: mean squared error over all nodes of the batch. The gradient
-treats bf as the identity (straight-through), so the mix gradients use the rounded operands.
+the CUDA path rounds from. The bf16 operands are those of the contractions that run on bf16 tensor cores
+(the channel-mixing layers, and the two contractions over the mesh of the truncated transforms) and of
+the per-mode mix. Loss: mean squared error over all nodes of the batch. The gradient treats bf as the
+identity (straight-through), so the mix gradients use the rounded operands.
 Parity: pinned by central finite differences of the loss (tests/test_oracle_sno.py), by the
 transform (S_M equals the leading rows of the oracle's sine matrix), and by gelu's closed forms.
 """
@@ -106,9 +108,11 @@ def forward(P: Params, u: np.ndarray, D, N: int, rounding: bool = True) -> tuple
         + P.bl[None, :, None, None]
     cache.h.append(h)
     for l in range(P.Wm.shape[0]):
-        hh = bf(np.einsum("py,bcyx,qx->bcpq", S, h, S))
+        T = np.einsum("bcyx,qx->bcyq", bf(h), bf(S))                  # contraction over x, bf16 operands
+        hh = bf(np.einsum("py,bcyq->bcpq", S, T))
         gh = np.einsum("pqoc,bcpq->bopq", bf(P.Wm[l]), hh)
-        z = np.einsum("py,bopq,qx->boyx", S, gh, S) + np.einsum("oc,bcyx->boyx", P.Wp[l], h) \
+        Tf = np.einsum("bopq,qx->bopx", gh, S)
+        z = np.einsum("py,bopx->boyx", bf(S), bf(Tf)) + np.einsum("oc,bcyx->boyx", bf(P.Wp[l]), bf(h)) \
             + P.bp[l][None, :, None, None]
         h = gelu(z)
         cache.hh.append(hh)

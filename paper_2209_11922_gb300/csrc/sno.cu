@@ -14,6 +14,7 @@
 #include "../../include/etd.h"
 #include "../../include/etd_sno.h"
 #include "sno_kernels.cuh"
+#include "sno_mma.cuh"
 
 void etd_internal_set_error(const char* msg);   // etd_api.cu
 
@@ -74,6 +75,11 @@ struct etd_sno_s {
   long long part_len = 0;
   double* lpart = nullptr; // loss partials
   int lblocks = 0;
+  // forward contractions on the tensor cores (BF16 operands, FP32 accumulation) when every K and output
+  // width fits a tile (n, C <= 256); the backward keeps FP32 (the exact straight-through gradient)
+  bool tc = false;
+  int num_sms = 148;
+  int* err = nullptr;      // set by a tensor-core kernel whose wait ran out
 };
 
 namespace {
@@ -120,6 +126,37 @@ struct GemmOp {
   }
 };
 
+// ---- tensor-core contractions (sno_mma.cuh): NCOL >= the output columns, K <= 256
+template <int NCOL, int EPI>
+etd_status mma_launch(const MmaArgs& g, int num_sms, cudaStream_t s) {
+  const size_t smem = mma_smem_bytes(NCOL, g.kpad);
+  static bool attr_set = false;   // one kernel per (NCOL, EPI); the largest size any call can ask for
+  if (!attr_set) {
+    SNO_CUDA(cudaFuncSetAttribute(sno_mma_kernel<NCOL, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024));
+    attr_set = true;
+  }
+  // CTAs per SM: at most 512 / NCOL (tensor-memory columns; a CTA that cannot allocate would wait for
+  // a co-resident one to finish), at most 16 (threads); the launch asks for enough shared memory that
+  // no more fit, and the grid covers that many per SM (CTAs loop over tiles)
+  const int per_sm = std::min(16, 512 / NCOL);
+  const size_t floor_bytes = (size_t)228 * 1024 / (per_sm + 1) + 1024;
+  const size_t launch_smem = std::max(smem, per_sm < 16 ? floor_bytes : (size_t)0);
+  const long long tiles = (long long)g.tiles_per_img * g.imgs;
+  const int fit = (int)std::min<size_t>(per_sm, (size_t)227 * 1024 / launch_smem);
+  const int grid = (int)std::min<long long>(tiles, (long long)std::max(1, fit) * num_sms);
+  sno_mma_kernel<NCOL, EPI><<<grid, 128, launch_smem, s>>>(g);
+  SNO_CUDA(cudaGetLastError());
+  return ETD_OK;
+}
+template <int EPI>
+etd_status mma_run(const MmaArgs& g, int num_sms, cudaStream_t s) {
+  if (g.ncol <= 32) return mma_launch<32, EPI>(g, num_sms, s);
+  if (g.ncol <= 64) return mma_launch<64, EPI>(g, num_sms, s);
+  if (g.ncol <= 128) return mma_launch<128, EPI>(g, num_sms, s);
+  return mma_launch<256, EPI>(g, num_sms, s);
+}
+
 #define SNO_TRY(x)                     \
   do {                                 \
     etd_status st_ = (x);              \
@@ -127,9 +164,30 @@ struct GemmOp {
   } while (0)
 
 // out (M x M per image) = S_M X S_M^T for `imgs` images X (n x n); T is scratch (n x M per image).
-// round: bf16-round the result.
-etd_status modes_of(const etd_sno_s* m, const float* X, int imgs, float* out, bool round, cudaStream_t s) {
+// round: bf16-round the result. tc: the first contraction (X S_M^T, K = n) on the tensor cores with
+// bf16 X and S_M, T then stored [M][n] per image.
+etd_status modes_of(const etd_sno_s* m, const float* X, int imgs, float* out, bool round, bool tc, cudaStream_t s) {
   const int n = m->n, M = m->M;
+  if (tc) {
+    MmaArgs g;
+    memset(&g, 0, sizeof(g));
+    g.tiles_per_img = (n + 127) / 128;
+    g.imgs = imgs;
+    g.rows = n;
+    g.kvalid = n;
+    g.kpad = (n + 31) / 32 * 32;
+    g.ncol = M;
+    g.A = X;  g.a_rs = n;  g.a_ks = 1;  g.a_is = (long long)n * n;      // A[i][j] = X[i][j]
+    g.B = m->S;  g.b_cs = n;  g.b_ks = 1;                               // B[m][j] = S_M[m][j]
+    g.C = m->T;  g.c_rs = 1;  g.c_cs = n;  g.c_is = (long long)M * n;  // T[m][i]
+    g.err = m->err;
+    SNO_TRY(mma_run<ME_STORE>(g, m->num_sms, s));
+    // out = S_M T^T  (M x M)
+    GemmOp o(M, M, n, imgs);
+    o.A(m->S, n, 1, 0).B(m->T, 1, n, (long long)M * n).Cm(out, M, 1, (long long)M * M);
+    o.g.round_c = round ? 1 : 0;
+    return o.run(s);
+  }
   // T = X S_M^T  (n x M)
   SNO_TRY(GemmOp(n, M, n, imgs).A(X, n, 1, (long long)n * n).B(m->S, 1, n, 0).Cm(m->T, M, 1, (long long)n * M).run(s));
   // out = S_M T  (M x M)
@@ -140,10 +198,28 @@ etd_status modes_of(const etd_sno_s* m, const float* X, int imgs, float* out, bo
 }
 
 // out (n x n per image) (+)= S_M^T Y S_M for `imgs` images Y (M x M); T is scratch (M x n per image).
-etd_status field_of(const etd_sno_s* m, const float* Y, int imgs, float* out, float beta, cudaStream_t s) {
+// tc: the second contraction (S_M^T T, K = M) on the tensor cores with bf16 S_M and T.
+etd_status field_of(const etd_sno_s* m, const float* Y, int imgs, float* out, float beta, bool tc, cudaStream_t s) {
   const int n = m->n, M = m->M;
   // T = Y S_M  (M x n)
   SNO_TRY(GemmOp(M, n, M, imgs).A(Y, M, 1, (long long)M * M).B(m->S, n, 1, 0).Cm(m->T, n, 1, (long long)M * n).run(s));
+  if (tc) {
+    // out[i][j] = sum_m S_M[m][i] T[m][j], as D[j][i] over tiles of 128 j
+    MmaArgs g;
+    memset(&g, 0, sizeof(g));
+    g.tiles_per_img = (n + 127) / 128;
+    g.imgs = imgs;
+    g.rows = n;
+    g.kvalid = M;
+    g.kpad = (M + 31) / 32 * 32;
+    g.ncol = n;
+    g.A = m->T;  g.a_rs = 1;  g.a_ks = n;  g.a_is = (long long)M * n;  // A[j][m] = T[m][j]
+    g.B = m->S;  g.b_cs = 1;  g.b_ks = n;                              // B[i][m] = S_M[m][i]
+    g.C = out;  g.c_rs = 1;  g.c_cs = n;  g.c_is = (long long)n * n;   // out[i][j]
+    g.beta = beta;
+    g.err = m->err;
+    return beta != 0.f ? mma_run<ME_ACCUM>(g, m->num_sms, s) : mma_run<ME_STORE>(g, m->num_sms, s);
+  }
   // out = S_M^T T  (n x n)
   GemmOp o(n, n, M, imgs);
   o.A(m->S, 1, n, 0).B(m->T, n, 1, (long long)M * n).Cm(out, n, 1, (long long)n * n);
@@ -174,6 +250,7 @@ void sno_free(etd_sno_s* m) {
   for (float* p : m->z) cudaFree(p);
   for (float* p : m->hh) cudaFree(p);
   if (m->lpart) cudaFree(m->lpart);
+  if (m->err) cudaFree(m->err);
   if (m->ahost) cudaFreeHost(m->ahost);
   delete m;
 }
@@ -181,6 +258,17 @@ void sno_free(etd_sno_s* m) {
 etd_status sno_alloc(float** p, long long count) {
   SNO_CUDA(cudaMalloc(p, (size_t)count * sizeof(float)));
   SNO_CUDA(cudaMemset(*p, 0, (size_t)count * sizeof(float)));
+  return ETD_OK;
+}
+
+// Reads (and clears) the error word of the tensor-core kernels; call after synchronising.
+etd_status check_err(etd_sno_s* m) {
+  int e = 0;
+  SNO_CUDA(cudaMemcpy(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    SNO_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    return sfail(ETD_ERR_TIMEOUT, "a tensor-core contraction of the operator gave up waiting for its MMAs");
+  }
   return ETD_OK;
 }
 
@@ -192,7 +280,7 @@ etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStre
                                                                                m->W + m->obl, m->h[0], B, C, np);
   SNO_CUDA(cudaGetLastError());
   for (int l = 0; l < L; ++l) {
-    SNO_TRY(modes_of(m, m->h[l], B * C, m->hh[l], true, s));
+    SNO_TRY(modes_of(m, m->h[l], B * C, m->hh[l], true, m->tc, s));
     // gh[b][o][m] = sum_c bf(Wm[l][m][o][c]) hh[b][c][m], batched over modes m
     {
       GemmOp o(B, C, C, (int)M2);
@@ -201,9 +289,26 @@ etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStre
       o.g.round_b = 1;
       SNO_TRY(o.run(s));
     }
-    SNO_TRY(field_of(m, m->gh, B * C, m->z[l], 0.f, s));
+    SNO_TRY(field_of(m, m->gh, B * C, m->z[l], 0.f, m->tc, s));
     // z[b] += Wp[l] h_l[b] + bp[l]; h_{l+1} = gelu(z)
-    {
+    if (m->tc) {
+      MmaArgs g;   // z[b][o][i] += sum_c bf(Wp[o][c]) bf(h[b][c][i]) + bp[o], as D[i][o] over tiles of 128 i
+      memset(&g, 0, sizeof(g));
+      g.tiles_per_img = (int)((np + 127) / 128);
+      g.imgs = B;
+      g.rows = (int)np;
+      g.kvalid = C;
+      g.kpad = (C + 31) / 32 * 32;
+      g.ncol = C;
+      g.A = m->h[l];  g.a_rs = 1;  g.a_ks = np;  g.a_is = img;
+      g.B = m->W + m->oWp + (long long)l * C * C;  g.b_cs = C;  g.b_ks = 1;
+      g.C = m->z[l];  g.c_rs = 1;  g.c_cs = np;  g.c_is = img;
+      g.beta = 1.f;
+      g.bias = m->W + m->obp + (long long)l * C;
+      g.C2 = m->h[l + 1];
+      g.err = m->err;
+      SNO_TRY(mma_run<ME_PW_GELU>(g, m->num_sms, s));
+    } else {
       GemmOp o(C, (int)np, C, B);
       o.A(m->W + m->oWp + (long long)l * C * C, C, 1, 0).B(m->h[l], np, 1, img).Cm(m->z[l], np, 1, img);
       o.g.beta = 1.f;
@@ -265,7 +370,7 @@ etd_status sno_backward(etd_sno_s* m, const float* u, int B, cudaStream_t s) {
       SNO_CUDA(cudaGetLastError());
     }
     // spectral path: dgh = S_M dz S_M^T
-    SNO_TRY(modes_of(m, dz, B * C, m->dgh, false, s));
+    SNO_TRY(modes_of(m, dz, B * C, m->dgh, false, false, s));
     // dWm[l][m][o][c] = sum_b dgh[b][o][m] hh[b][c][m]
     SNO_TRY(GemmOp(C, C, B, (int)M2)
                 .A(m->dgh, M2, C * M2, 1)
@@ -283,7 +388,7 @@ etd_status sno_backward(etd_sno_s* m, const float* u, int B, cudaStream_t s) {
     // dh_l = Wp^T dz + S_M^T dhh S_M
     SNO_TRY(GemmOp(C, (int)np, C, B).A(m->W + m->oWp + (long long)l * C * C, 1, C, 0).B(dz, np, 1, img)
                 .Cm(dn, np, 1, img).run(s));
-    SNO_TRY(field_of(m, m->gh, B * C, dn, 1.f, s));
+    SNO_TRY(field_of(m, m->gh, B * C, dn, 1.f, false, s));
     float* t = dh;
     dh = dn;
     dn = t;
@@ -365,6 +470,12 @@ etd_status etd_sno_create(etd_sno* out, int N, int C, int M, int L, int max_batc
           (float)(std::sqrt(2.0 / N) * std::sin(M_PI * (double)(((long long)(p + 1) * (j + 1)) % (2LL * N)) / N));
   if (cudaMemcpy(m->S, hs.data(), hs.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(sfail(ETD_ERR_CUDA, "upload of the mode matrix"));
+  m->tc = m->n <= 256 && C <= 256 && M <= 256;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMalloc(&m->err, sizeof(int)) != cudaSuccess || cudaMemset(m->err, 0, sizeof(int)) != cudaSuccess)
+    return bail(sfail(ETD_ERR_OOM, "error word"));
   *out = m;
   return ETD_OK;
 }
@@ -420,6 +531,7 @@ etd_status etd_sno_train_step(etd_sno m, const float* u, const double* D, const 
   std::vector<double> lp(m->lblocks);
   SNO_CUDA(cudaMemcpyAsync(lp.data(), m->lpart, m->lblocks * sizeof(double), cudaMemcpyDeviceToHost, s));
   SNO_CUDA(cudaStreamSynchronize(s));
+  SNO_TRY(check_err(m));
   if (loss) {
     double t = 0.0;
     for (double v : lp) t += v;
@@ -540,44 +652,59 @@ etd_status etd_parareal_run(etd_parareal p, const float* u0, float* u_out, int m
     SNO_CUDA(cudaMemcpyAsync(win(p->U, n + 1), win(p->Go, n), fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
   }
   std::vector<double> hp((size_t)B * p->nblk * 2);
-  for (int k = 1; k <= max_iter; ++k) {
+  // U_0 .. U_d are the fine solution itself: U_0 = u0, and each iteration makes at least one more window
+  // exact (the window after the exact prefix takes F of an exact start; a fallback from an exact start
+  // extends the prefix too). Those windows keep their values: in exact arithmetic the Parareal update
+  // gives them F(U_n) anyway, and recomputing G(U_n^{k+1}) - G(U_n^k) there would only add the coarse
+  // propagator's rounding (bf16 in the operator, not Lipschitz in its input) to converged states.
+  int d = 0;
+  for (int k = 1; k <= max_iter && d < W; ++k) {
     // fine propagation of every window of the current iterate, in one batched run
     SNO_CUDA(cudaMemcpyAsync(p->F, p->U, W * fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
     for (int i = 0; i < W * B; ++i) p->ptr_all[i] = p->F + (size_t)i * p->npix;
     SNO_TRY(etd_batch_run(p->fine_all, p->ptr_all.data(), p->steps, s));
     // sequential correction sweep
-    SNO_CUDA(cudaMemcpyAsync(p->V, u0, fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    SNO_CUDA(cudaMemcpyAsync(p->V, p->U, (size_t)(d + 1) * fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
     double worst = 0.0;
-    for (int n = 0; n < W; ++n) {
-      SNO_TRY(coarse_apply(p, win(p->V, n), p->Gn, s));
-      parareal_update_kernel<<<dim3(p->nblk, B), 256, 0, s>>>(p->Gn, win(p->F, n), win(p->Go, n), win(p->U, n + 1),
-                                                             win(p->V, n + 1), p->npix, p->part);
+    int dn = d;
+    for (int n = d; n < W; ++n) {
+      const bool exact_start = n == d;   // U_n = V_n is the fine solution: V_{n+1} = F(U_n)
+      if (!exact_start) SNO_TRY(coarse_apply(p, win(p->V, n), p->Gn, s));
+      parareal_update_kernel<<<dim3(p->nblk, B), 256, 0, s>>>(exact_start ? nullptr : p->Gn, win(p->F, n),
+                                                             win(p->Go, n), win(p->U, n + 1), win(p->V, n + 1),
+                                                             p->npix, p->part);
       SNO_CUDA(cudaGetLastError());
-      SNO_CUDA(cudaMemcpyAsync(win(p->Go, n), p->Gn, fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      if (!exact_start)
+        SNO_CUDA(cudaMemcpyAsync(win(p->Go, n), p->Gn, fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
       SNO_CUDA(cudaMemcpyAsync(hp.data(), p->part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       SNO_CUDA(cudaStreamSynchronize(s));
       double corr = 0.0;
       for (int b = 0; b < B; ++b) {
-        double a = 0.0, d = 0.0;
+        double a = 0.0, e2 = 0.0;
         for (int j = 0; j < p->nblk; ++j) {
           a += hp[((size_t)b * p->nblk + j) * 2];
-          d += hp[((size_t)b * p->nblk + j) * 2 + 1];
+          e2 += hp[((size_t)b * p->nblk + j) * 2 + 1];
         }
-        corr = std::max(corr, a > 0 ? std::sqrt(d / a) : std::sqrt(d));
+        corr = std::max(corr, a > 0 ? std::sqrt(e2 / a) : std::sqrt(e2));
       }
-      if (k > 1 && corr > fallback_tol) {   // rejected: advance this window with the plain solver
+      if (exact_start) {
+        dn = n + 1;
+      } else if (k > 1 && corr > fallback_tol) {   // rejected: advance this window with the plain solver
         SNO_TRY(fine_one(p, win(p->V, n), win(p->V, n + 1), s));
         st.fallbacks += 1;
+        if (dn == n) dn = n + 1;
       }
       worst = std::max(worst, corr);
     }
     std::swap(p->U, p->V);
+    d = dn;
     st.iterations = k;
     st.correction[k - 1] = worst;
     if (worst < tol) break;
   }
   SNO_CUDA(cudaMemcpyAsync(u_out, win(p->U, W), fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
   SNO_CUDA(cudaStreamSynchronize(s));
+  if (p->sno) SNO_TRY(check_err(p->sno));
   if (stats) *stats = st;
   return ETD_OK;
 }

@@ -234,8 +234,9 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
   }
 }
 
-// Parareal update V = Gn + F - Go, and per-problem squared norms of V and of V - U (FP64 partials,
-// one block row per problem: blockIdx.y = problem)
+// Parareal update V = Gn + F - Go (V = F where Gn is NULL: a window from a start that is already the
+// fine solution), and per-problem squared norms of V and of V - U (FP64 partials, one block row per
+// problem: blockIdx.y = problem)
 __global__ void __launch_bounds__(256) parareal_update_kernel(const float* __restrict__ Gn, const float* __restrict__ F,
                                                               const float* __restrict__ Go, const float* __restrict__ U,
                                                               float* __restrict__ V, long long npix,
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(256) parareal_update_kernel(const float* __res
   const long long base = (long long)blockIdx.y * npix;
   double a = 0.0, d = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
-    const float v = Gn[base + i] + F[base + i] - Go[base + i];
+    const float v = Gn ? Gn[base + i] + F[base + i] - Go[base + i] : F[base + i];
     V[base + i] = v;
     const float e = v - U[base + i];
     a += (double)v * v;
