@@ -316,7 +316,7 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   }
   a.P = P;
   a.lp = pair_stride(*k, P);
-  L.fn = k->fn;
+  L.fn = (op >= 0 && op < 9 && k->fn_op[op]) ? k->fn_op[op] : k->fn;
   L.grid = dim3((unsigned)grid);
   L.block = dim3((unsigned)(P * k->tpp));
   L.smem = pass_smem_bytes(*k, P, two ? 2 : 1);
@@ -331,7 +331,7 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
   if (L.smem > (size_t)optin) return fail(ETD_ERR_UNSUPPORTED, "tile needs %zu B of shared memory (max %d)", L.smem, optin);
   if (L.smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaError_t e = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "cudaFuncSetAttribute(%d B): %s", optin, cudaGetErrorString(e));
   }
   return ETD_OK;

@@ -112,7 +112,10 @@ template <class T> __device__ __forceinline__ void count_step(const PassArgs<T>&
   }
 }
 
-template <class T, int N, int VAR>
+// OPC: the pass operation fixed at compile time (one of PassOp), or -1 to take it from A.op. A kernel
+// with a fixed operation holds only that operation's code, so the instructions a launch executes lie
+// together (fewer instruction-cache misses than in the kernel that serves every operation).
+template <class T, int N, int VAR, int OPC = -1>
 __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) {
   using L = PairLayout<T, N, VAR>;
   constexpr bool PER = L::HART;   // periodic: no boundary planes, rows or slots
@@ -127,7 +130,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   const C* __restrict__ tw = tws;
   const T* __restrict__ sn = A.sn;
   C* b0 = tws + ((TWN + 1) & ~1);
-  const int op = A.op;
+  const int op = OPC >= 0 ? OPC : A.op;
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
   C* b1 = b0 + A.P * LP;
   C* scr = b0 + (two ? 2 : 1) * A.P * LP;
@@ -524,6 +527,19 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(cons
   pass_body<T, N, VAR>(A, (int)blockIdx.x);
 }
 
+// The same with the operation fixed (A.op must equal OPC).
+template <class T, int N, int VAR, int OPC>
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel_op(const PassArgs<T> A) {
+  pass_body<T, N, VAR, OPC>(A, (int)blockIdx.x);
+}
+
+// Shapes with kernels per operation for the passes of a time step (REACT, TRANSFORM, RK1, S1, S2):
+// the FP32 lengths of the large 2D and 3D workloads.
+template <class T, int N, int VAR> constexpr bool pass_op_kernels() {
+  return sizeof(T) == 4 && ((VAR == V_ODD && (N == 1024 || N == 2048)) || (VAR == V_REC && N == 256) ||
+                            (VAR == V_HART && N == 128));
+}
+
 // Batches: one launch covers the tiles of many independent problems whose transformed axis has
 // length N. CTA b works on tile map[b].y of the problem described by descs[map[b].x]; entry and exit
 // passes take the caller's field pointer from user[descs[.].user_slot].
@@ -543,6 +559,7 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
 struct KernelInfo {
   const void* fn;
   const void* fn_batched;
+  const void* fn_op[9];   // kernels with the operation fixed, by PassOp (NULL: use fn)
   int N;
   int tpp;
   int lp;
@@ -563,8 +580,17 @@ template <int... Rs> void radix_list(int* out, Radices<Rs...>) {
 template <class T, int N, int VAR> KernelInfo kernel_info() {
   using L = PairLayout<T, N, VAR>;
   KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, VAR>),
-               reinterpret_cast<const void*>(&pass_kernel_batched<T, N, VAR>), N, L::TPP, L::LP, (int)sizeof(T), L::M,
+               reinterpret_cast<const void*>(&pass_kernel_batched<T, N, VAR>),
+               {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+               N, L::TPP, L::LP, (int)sizeof(T), L::M,
                VAR, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
+  if constexpr (pass_op_kernels<T, N, VAR>()) {
+    k.fn_op[OP_REACT] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_REACT>);
+    k.fn_op[OP_TRANSFORM] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_TRANSFORM>);
+    k.fn_op[OP_RK1] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_RK1>);
+    k.fn_op[OP_S1] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S1>);
+    k.fn_op[OP_S2] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S2>);
+  }
   radix_list(k.radix, typename L::Plan::R{});
   return k;
 }
