@@ -328,7 +328,8 @@ def run_gb300(args, w):
 
 def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
     """Many independent 2D problems advanced by one batch (grouped launches), against the same
-    problems advanced one plan each (the plain GPU solver). Returns the measured figures."""
+    problems advanced one plan each (the plain GPU solver). Returns the measured figures, with the
+    steady-state schedule the batch chose at creation and both schedules' trial times."""
     import torch
 
     from paper_2209_11922_gb300.etd import Batch, Plan
@@ -353,6 +354,7 @@ def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
     batch = Batch([p[0] for p in probs], [p[1] for p in probs], bw.tau, 2, dtype, route=args.route)
     create_s = time.perf_counter() - t0
     info = batch.info()
+    sched = batch.schedule()
 
     def timed(fn, k):
         tot = 0.0
@@ -390,7 +392,8 @@ def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
     return {"workload": bw.name, "problems": len(probs), "unknowns": unknowns, "time_steps_per_run": nsteps,
             "value": value, "unit": UNIT, "ms_per_run": ms / steps, "plans_value": value_plans,
             "speedup_vs_plans": value / value_plans, "launches_per_time_step": info["launches_per_step"],
-            "tuned_tile_pairs": info["tile_pairs"], "create_s": round(create_s, 3), "runs_timed": steps,
+            "tuned_tile_pairs": info["tile_pairs"], "schedule": sched, "create_s": round(create_s, 3),
+            "runs_timed": steps,
             "gpu_launches": steps * (info["launches_per_step"] * nsteps + 12),
             "roofline": {"bound": "hbm", "kernel": "one time step (all grouped launches)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
@@ -412,7 +415,8 @@ def run_batched(args, bw):
         "config": {"workload": bw.name, "problems": m["problems"], "unknowns": m["unknowns"],
                    "time_steps_per_step": m["time_steps_per_run"], "tau": bw.tau, "scheme": "ETDRK2",
                    "launches_per_time_step": m["launches_per_time_step"], "tuned_tile_pairs": m["tuned_tile_pairs"],
-                   "create_s": m["create_s"], "l2": "256 MiB buffer written between bench steps"},
+                   "schedule": m["schedule"], "create_s": m["create_s"],
+                   "l2": "256 MiB buffer written between bench steps"},
         "gpu_launches": m["gpu_launches"], "plans_value": m["plans_value"],
         "speedup_vs_plans": m["speedup_vs_plans"], "roofline": m["roofline"], "clocks": clk.summary(),
     }

@@ -101,7 +101,9 @@ typedef struct {
                         pass of every etd_run withholds its accumulator-ready signal, so that pass's
                         epilogue warps wait out their 2 s limit, abort and set the plan's error word;
                         the next synchronising call returns ETD_ERR_TIMEOUT and that run's field is
-                        invalid. Tests the failure path; any other value is ignored. */
+                        invalid. Tests the failure path. ETD_DEBUG_BATCH_SERIAL / ETD_DEBUG_BATCH_PARALLEL
+                        (batches): take that steady-state schedule instead of timing both at creation.
+                        Any other value is ignored. */
   int bc;            /* boundary condition of every axis: ETD_BC_DIRICHLET (default) or ETD_BC_PERIODIC */
   double flog;       /* coefficient of artanh(u) = (1/2) ln((1+u)/(1-u)) in f; default 0. Nonzero values
                         run on periodic plans and batches (any route) and on the GEMM routes; a Dirichlet
@@ -110,6 +112,8 @@ typedef struct {
                         etd_monitor reports). */
 } etd_options;
 #define ETD_DEBUG_STALL_FIRST_GEMM_PASS 0x5A11
+#define ETD_DEBUG_BATCH_SERIAL 0x5A12
+#define ETD_DEBUG_BATCH_PARALLEL 0x5A13
 #define ETD_BC_DIRICHLET 0
 #define ETD_BC_PERIODIC 1
 
@@ -284,7 +288,11 @@ etd_status etd_destroy(etd_plan plan);
  * Each pass of a time step is one kernel launch per distinct length of the transformed axis,
  * covering every problem with that length; the tile size of each launch is tuned at creation by
  * timing the candidates (set ETD_AUTOTUNE=0 to take a fixed choice). Steady-state steps replay as a
- * CUDA graph. Results equal those of one plan per problem with the same options up to rounding
+ * CUDA graph in one of two schedules: the launches of a pass one after another on one stream, each
+ * overlapping its predecessor's tail (programmatic dependent launch), or as parallel graph branches
+ * (they cover disjoint problems) joined before the next pass. Creation times both graphs on the
+ * workspace and keeps the faster (etd_batch_schedule reports the choice and both times); with
+ * ETD_AUTOTUNE=0 the serial schedule is taken. Results equal those of one plan per problem with the same options up to rounding
  * (the batched kernel is a separate instantiation, so the compiler may contract and order the
  * floating-point operations differently; measured differences are at the dtype's rounding level).
  * Allocates per-problem fields and tables on the current device. Errors as for etd_plan_create;
@@ -304,6 +312,12 @@ etd_status etd_batch_run(etd_batch b, void* const* u, int64_t nsteps, void* stre
 /* Total unknowns, launches per time step, and the tuned pencil pairs per tile of the first
  * max_groups step launches (any pointer may be NULL). */
 etd_status etd_batch_info(etd_batch b, int64_t* unknowns, int* launches_per_step, int* tile_pairs, int max_groups);
+
+/* The steady-state schedule chosen at creation: *parallel = 1 for parallel graph branches per pass,
+ * 0 for the serial stream; *us_serial and *us_parallel = the creation-time trial's microseconds per
+ * time step of each (0 where no trial ran: a single launch per pass, ETD_AUTOTUNE=0, or a forced
+ * schedule). Any pointer may be NULL. */
+etd_status etd_batch_schedule(etd_batch b, int* parallel, double* us_serial, double* us_parallel);
 
 /* Release a batch. NULL is accepted. */
 etd_status etd_batch_destroy(etd_batch b);

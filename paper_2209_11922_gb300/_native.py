@@ -19,6 +19,8 @@ c_int, c_double, c_int64, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, c
 
 ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_UNSUPPORTED, ETD_ERR_CUDA, ETD_ERR_OOM, ETD_ERR_NONFINITE, ETD_ERR_TIMEOUT = range(7)
 ETD_DEBUG_STALL_FIRST_GEMM_PASS = 0x5A11
+ETD_DEBUG_BATCH_SERIAL = 0x5A12
+ETD_DEBUG_BATCH_PARALLEL = 0x5A13
 ETD_F64, ETD_F32 = 0, 1
 ETD_ROUTE_AUTO, ETD_ROUTE_FFT, ETD_ROUTE_FFT_HALF, ETD_ROUTE_GEMM_TF32, ETD_ROUTE_GEMM_BF16X3, ETD_ROUTE_FFT_SPLIT = 0, 1, 2, 3, 4, 5
 ETD_BC_DIRICHLET, ETD_BC_PERIODIC = 0, 1
@@ -69,6 +71,7 @@ _SIGS = {
                                  ctypes.POINTER(c_double), c_double, c_int, ctypes.POINTER(EtdOptions)]),
     "etd_batch_run": (c_int, [c_void_p, ctypes.POINTER(c_void_p), c_int64, c_void_p]),
     "etd_batch_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int]),
+    "etd_batch_schedule": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "etd_batch_destroy": (c_int, [c_void_p]),
     "etd_monitor_noalloc": (c_int, [c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), c_double, c_int,
                                     c_void_p, c_void_p, c_void_p]),

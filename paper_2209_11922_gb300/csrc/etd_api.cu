@@ -1054,6 +1054,7 @@ etd_status run_steps(etd_plan_s* pl, int64_t nsteps, cudaStream_t s) {
 struct BatchGroup {
   const void* fn = nullptr;     // pass_kernel_batched<T, N, ODD>
   int axis = 0, op = 0, N = 0, P = 1, nbuf = 1, kind = 0;
+  int pass = 0;                 // index of the pass in the time step (groups of one pass are independent)
   size_t smem = 0;
   int nctas = 0, tpp = 1;
   std::vector<int> inst;        // problems in this group
@@ -1084,6 +1085,14 @@ struct etd_batch_s {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  // Steady-state schedule: the groups of a pass one after another on one stream with programmatic
+  // dependent launch (0), or as parallel graph branches joined before the next pass (1). Chosen at
+  // creation by timing both graphs (trial_us: microseconds per step, serial / parallel).
+  int concurrent = 0;
+  double trial_us[2] = {0.0, 0.0};
+  std::vector<cudaStream_t> side;   // capture streams of the parallel branches
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
 };
 
 namespace {
@@ -1161,7 +1170,7 @@ etd_status batch_group_upload(etd_batch_s* b, const std::vector<BatchTables>& ta
   return ETD_OK;
 }
 
-etd_status batch_launch(const etd_batch_s* b, const BatchGroup& g, cudaStream_t s) {
+etd_status batch_launch(const etd_batch_s* b, const BatchGroup& g, cudaStream_t s, bool pdl = true) {
   static const int use_pdl = env_int("ETD_PDL", 1);
   void* user = b->d_user;
   void* argv[3] = {const_cast<void**>(&g.d_descs), const_cast<void**>(&g.d_map), &user};
@@ -1174,7 +1183,7 @@ etd_status batch_launch(const etd_batch_s* b, const BatchGroup& g, cudaStream_t 
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = use_pdl ? 1 : 0;
+  cfg.numAttrs = (use_pdl && pdl) ? 1 : 0;
   cudaError_t e = cudaLaunchKernelExC(&cfg, g.fn, argv);
   if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batched kernel launch: %s", cudaGetErrorString(e));
   return ETD_OK;
@@ -1203,7 +1212,7 @@ etd_status batch_build_op(etd_batch_s* b, const std::vector<BatchTables>& tabs, 
     const int odd = o.axis == 0 ? b->oddx[g.inst[0]] : b->oddy[g.inst[0]];
     const KernelInfo* k = find_pass_kernel((int)sizeof(T), g.N, odd);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", g.N);
-    g.fn = k->fn_batched;
+    g.fn = (o.op >= 0 && o.op < 9 && k->fn_batched_op[o.op]) ? k->fn_batched_op[o.op] : k->fn_batched;
     g.tpp = k->tpp;
     long long unk = 0;
     const int cut = b->periodic ? 0 : 1;
@@ -1271,6 +1280,112 @@ etd_status batch_build_op(etd_batch_s* b, const std::vector<BatchTables>& tabs, 
   return ETD_OK;
 }
 
+// Captures G steady-state time steps into an executable graph. Serial schedule: every group on one
+// stream, each launch with programmatic dependent launch on its predecessor. Parallel schedule: the
+// groups of a pass (disjoint problems) as parallel branches forked from and joined into the capture
+// stream, so a pass takes the time of its slowest group rather than the sum; no programmatic edges
+// (the pass kernels' dependency wait then returns at once).
+etd_status batch_capture(etd_batch_s* b, int G, bool parallel, cudaGraphExec_t* out) {
+  *out = nullptr;
+  if (!b->cap_stream) ETD_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  size_t widest = 1;
+  for (size_t i = 0, j; i < b->step.size(); i = j) {
+    for (j = i; j < b->step.size() && b->step[j].pass == b->step[i].pass; ++j) {}
+    widest = std::max(widest, j - i);
+  }
+  if (parallel) {
+    while (b->side.size() < widest) {
+      cudaStream_t ss = nullptr;
+      ETD_CUDA(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking));
+      b->side.push_back(ss);
+    }
+    if (!b->ev_fork) ETD_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    while (b->ev_join.size() < widest) {
+      cudaEvent_t ev = nullptr;
+      ETD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      b->ev_join.push_back(ev);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  ETD_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  etd_status st = ETD_OK;
+  cudaError_t ce = cudaSuccess;
+  for (int k = 0; k < G && st == ETD_OK && ce == cudaSuccess; ++k) {
+    for (size_t i = 0, j; i < b->step.size() && st == ETD_OK && ce == cudaSuccess; i = j) {
+      for (j = i; j < b->step.size() && b->step[j].pass == b->step[i].pass; ++j) {}
+      if (!parallel || j - i == 1) {
+        for (size_t q = i; q < j && st == ETD_OK; ++q) st = batch_launch(b, b->step[q], b->cap_stream, !parallel);
+        continue;
+      }
+      if ((ce = cudaEventRecord(b->ev_fork, b->cap_stream)) != cudaSuccess) break;
+      for (size_t q = i; q < j; ++q) {
+        cudaStream_t ss = b->side[q - i];
+        if ((ce = cudaStreamWaitEvent(ss, b->ev_fork, 0)) != cudaSuccess) break;
+        if ((st = batch_launch(b, b->step[q], ss, false)) != ETD_OK) break;
+        if ((ce = cudaEventRecord(b->ev_join[q - i], ss)) != cudaSuccess) break;
+        if ((ce = cudaStreamWaitEvent(b->cap_stream, b->ev_join[q - i], 0)) != cudaSuccess) break;
+      }
+    }
+  }
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+  if (st != ETD_OK || ce != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != ETD_OK) return st;
+    return fail(ETD_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : e));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+  return ETD_OK;
+}
+
+// Creation-time A/B of the two schedules (on the workspace, before any caller data): both graphs are
+// built and timed, the faster one is kept for the runs.
+etd_status batch_choose_schedule(etd_batch_s* b) {
+  const int G = env_int("ETD_GRAPH_STEPS", 32);
+  bool multi = false;
+  for (size_t q = 1; q < b->step.size(); ++q) multi = multi || b->step[q].pass == b->step[q - 1].pass;
+  if (G <= 0 || !multi) return ETD_OK;
+  cudaGraphExec_t gx[2] = {nullptr, nullptr};
+  etd_status st = ETD_OK;
+  for (int m = 0; m < 2 && st == ETD_OK; ++m) st = batch_capture(b, G, m == 1, &gx[m]);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == ETD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    st = fail(ETD_ERR_CUDA, "event create");
+  // alternate the schedules so that clock drift affects both alike; best of three per schedule
+  float best[2] = {1e30f, 1e30f};
+  for (int r = 0; r < 4 && st == ETD_OK; ++r)
+    for (int m = 0; m < 2 && st == ETD_OK; ++m) {
+      cudaError_t ce = cudaGraphLaunch(gx[m], b->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, b->cap_stream);
+      if (ce == cudaSuccess) ce = cudaGraphLaunch(gx[m], b->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) {
+        st = fail(ETD_ERR_CUDA, "schedule trial: %s", cudaGetErrorString(ce));
+        break;
+      }
+      if (r > 0) best[m] = std::min(best[m], ms);
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st == ETD_OK) {
+    const int pick = best[1] < best[0] ? 1 : 0;
+    b->trial_us[0] = 1e3 * best[0] / G;
+    b->trial_us[1] = 1e3 * best[1] / G;
+    b->concurrent = pick;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = gx[pick];
+    b->graph_steps = G;
+    gx[pick] = nullptr;
+  }
+  for (cudaGraphExec_t x : gx)
+    if (x) cudaGraphExecDestroy(x);
+  return st;
+}
+
 template <class T>
 etd_status batch_build(etd_batch_s* b) {
   // tables
@@ -1324,15 +1439,23 @@ etd_status batch_build(etd_batch_s* b) {
   }
   const bool autotune = env_int("ETD_AUTOTUNE", 1) != 0;
   std::map<long long, int> tuned;
-  for (const BatchOp& o : ops) {
-    etd_status st = batch_build_op<T>(b, tabs, o, b->step, aux, tuned, autotune);
+  for (size_t oi = 0; oi < ops.size(); ++oi) {
+    const size_t first = b->step.size();
+    etd_status st = batch_build_op<T>(b, tabs, ops[oi], b->step, aux, tuned, autotune);
     if (st != ETD_OK) return st;
+    for (size_t q = first; q < b->step.size(); ++q) b->step[q].pass = (int)oi;
   }
   const BatchOp ent{OP_ENTRY, 0, -1, -1, V, -1, PK_ENTRY_EXIT, 1, 2.0}, ext{OP_EXIT, 0, V, -1, -1, -1, PK_ENTRY_EXIT, 1, 2.0};
   etd_status st = batch_build_op<T>(b, tabs, ent, b->entry, aux, tuned, false);
   if (st != ETD_OK) return st;
   st = batch_build_op<T>(b, tabs, ext, b->exit_, aux, tuned, false);
   if (st != ETD_OK) return st;
+  if (b->opt.debug == ETD_DEBUG_BATCH_SERIAL || b->opt.debug == ETD_DEBUG_BATCH_PARALLEL) {
+    b->concurrent = b->opt.debug == ETD_DEBUG_BATCH_PARALLEL;
+  } else if (autotune) {
+    etd_status st2 = batch_choose_schedule(b);
+    if (st2 != ETD_OK) return st2;
+  }
   // the autotuner ran passes on the workspace: restore the zero state the boundary slots rely on
   ETD_CUDA(cudaMemset(b->ws, 0, b->ws_bytes));
   ETD_CUDA(cudaDeviceSynchronize());
@@ -1346,22 +1469,9 @@ etd_status batch_run_steps(etd_batch_s* b, int64_t nsteps, cudaStream_t s) {
     if (!b->graph || b->graph_steps != G) {
       if (b->graph) cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
-      if (!b->cap_stream) ETD_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
-      cudaGraph_t g = nullptr;
-      ETD_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-      etd_status st = ETD_OK;
-      for (int k = 0; k < G && st == ETD_OK; ++k)
-        for (const BatchGroup& grp : b->step)
-          if ((st = batch_launch(b, grp, b->cap_stream)) != ETD_OK) break;
-      cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
-      if (st != ETD_OK) {
-        if (g) cudaGraphDestroy(g);
-        return st;
-      }
-      if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&b->graph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(ETD_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+      b->graph_steps = 0;
+      etd_status st = batch_capture(b, G, b->concurrent != 0, &b->graph);
+      if (st != ETD_OK) return st;
       b->graph_steps = G;
     }
     for (; done + G <= nsteps; done += G) ETD_CUDA(cudaGraphLaunch(b->graph, s));
@@ -1950,10 +2060,21 @@ etd_status etd_batch_info(etd_batch b, int64_t* unknowns, int* launches_per_step
   return ETD_OK;
 }
 
+etd_status etd_batch_schedule(etd_batch b, int* parallel, double* us_serial, double* us_parallel) {
+  if (!b) return fail(ETD_ERR_INVALID_ARG, "batch is NULL");
+  if (parallel) *parallel = b->concurrent;
+  if (us_serial) *us_serial = b->trial_us[0];
+  if (us_parallel) *us_parallel = b->trial_us[1];
+  return ETD_OK;
+}
+
 etd_status etd_batch_destroy(etd_batch b) {
   if (!b) return ETD_OK;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaStream_t ss : b->side) cudaStreamDestroy(ss);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (cudaEvent_t ev : b->ev_join) cudaEventDestroy(ev);
   if (b->ws) cudaFree(b->ws);
   if (b->tables) cudaFree(b->tables);
   if (b->d_user) cudaFree(b->d_user);

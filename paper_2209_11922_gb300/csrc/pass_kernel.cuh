@@ -534,10 +534,12 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel_op(c
 }
 
 // Shapes with kernels per operation for the passes of a time step (REACT, TRANSFORM, RK1, S1, S2):
-// the FP32 lengths of the large 2D and 3D workloads.
+// the FP32 lengths of the large 2D and 3D workloads and of batches of meshes from 64 to 384.
 template <class T, int N, int VAR> constexpr bool pass_op_kernels() {
-  return sizeof(T) == 4 && ((VAR == V_ODD && (N == 1024 || N == 2048)) || (VAR == V_REC && N == 256) ||
-                            (VAR == V_HART && N == 128));
+  return sizeof(T) == 4 &&
+         ((VAR == V_ODD && (N == 1024 || N == 2048)) ||
+          (VAR == V_REC && (N == 64 || N == 96 || N == 128 || N == 192 || N == 256 || N == 384)) ||
+          (VAR == V_HART && N == 128));
 }
 
 // Batches: one launch covers the tiles of many independent problems whose transformed axis has
@@ -555,11 +557,21 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
   pass_body<T, N, VAR>(A, m.y);
 }
 
+// The same with the operation fixed (every descriptor's op must equal OPC).
+template <class T, int N, int VAR, int OPC>
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
+    pass_kernel_batched_op(const PassArgs<T>* __restrict__ descs, const int2* __restrict__ map, T* const* __restrict__) {
+  const int2 m = map[blockIdx.x];
+  PassArgs<T> A = descs[m.x];
+  pass_body<T, N, VAR, OPC>(A, m.y);
+}
+
 // Host-side description of one instantiation.
 struct KernelInfo {
   const void* fn;
   const void* fn_batched;
   const void* fn_op[9];   // kernels with the operation fixed, by PassOp (NULL: use fn)
+  const void* fn_batched_op[9];   // the same for batches (NULL: use fn_batched)
   int N;
   int tpp;
   int lp;
@@ -582,6 +594,7 @@ template <class T, int N, int VAR> KernelInfo kernel_info() {
   KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, VAR>),
                reinterpret_cast<const void*>(&pass_kernel_batched<T, N, VAR>),
                {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+               {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                N, L::TPP, L::LP, (int)sizeof(T), L::M,
                VAR, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
   if constexpr (pass_op_kernels<T, N, VAR>()) {
@@ -590,6 +603,11 @@ template <class T, int N, int VAR> KernelInfo kernel_info() {
     k.fn_op[OP_RK1] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_RK1>);
     k.fn_op[OP_S1] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S1>);
     k.fn_op[OP_S2] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S2>);
+    // batches are 2D: no TRANSFORM passes
+    k.fn_batched_op[OP_REACT] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_REACT>);
+    k.fn_batched_op[OP_RK1] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_RK1>);
+    k.fn_batched_op[OP_S1] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S1>);
+    k.fn_batched_op[OP_S2] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S2>);
   }
   radix_list(k.radix, typename L::Plan::R{});
   return k;

@@ -14,6 +14,8 @@ from . import _native as nat
 
 _DT = {"f64": nat.ETD_F64, "f32": nat.ETD_F32}
 _BC = {"dirichlet": nat.ETD_BC_DIRICHLET, "periodic": nat.ETD_BC_PERIODIC}
+# batch steady-state schedule: timed at creation ("auto") or forced
+_SCHEDULE = {"auto": 0, "serial": nat.ETD_DEBUG_BATCH_SERIAL, "parallel": nat.ETD_DEBUG_BATCH_PARALLEL}
 _ROUTE = {"auto": nat.ETD_ROUTE_AUTO, "fft": nat.ETD_ROUTE_FFT, "fft_half": nat.ETD_ROUTE_FFT_HALF,
           "gemm_tf32": nat.ETD_ROUTE_GEMM_TF32, "gemm_bf16x3": nat.ETD_ROUTE_GEMM_BF16X3,
           "fft_split": nat.ETD_ROUTE_FFT_SPLIT}
@@ -241,8 +243,10 @@ class Batch:
     def __init__(self, N: Sequence[Sequence[int]], D: Sequence[float], tau: float, scheme: int = 2,
                  dtype: str = "f32", h: Optional[Sequence[Sequence[float]]] = None, c2: float = 0.5,
                  flin: float = 1.0, fcub: float = -1.0, route: str = "auto", bc: str = "dirichlet",
-                 flog: float = 0.0):
+                 flog: float = 0.0, schedule: str = "auto"):
         L = nat.lib()
+        if schedule not in _SCHEDULE:
+            raise ValueError(f"schedule must be one of {sorted(_SCHEDULE)}")
         self.N = [tuple(int(v) for v in n) for n in N]
         self.count = len(self.N)
         self.h = [tuple(float(v) for v in x) for x in (h if h is not None else [(1.0 / a, 1.0 / b) for a, b in self.N])]
@@ -257,6 +261,7 @@ class Batch:
         if bc not in _BC:
             raise ValueError("bc must be 'dirichlet' or 'periodic'")
         opt.bc = _BC[bc]
+        opt.debug = _SCHEDULE[schedule]
         self.bc = bc
         Na = (ctypes.c_int64 * (2 * self.count))(*[v for n in self.N for v in n])
         ha = (ctypes.c_double * (2 * self.count))(*[v for x in self.h for v in x])
@@ -289,6 +294,15 @@ class Batch:
         tiles = (ctypes.c_int * 64)()
         nat.check(nat.lib().etd_batch_info(self._h, ctypes.byref(unk), ctypes.byref(nl), tiles, 64), "etd_batch_info")
         return {"unknowns": unk.value, "launches_per_step": nl.value, "tile_pairs": list(tiles[:min(nl.value, 64)])}
+
+    def schedule(self) -> dict:
+        """The steady-state schedule chosen at creation and the trial's microseconds per step of each."""
+        par = ctypes.c_int()
+        us = (ctypes.c_double(), ctypes.c_double())
+        nat.check(nat.lib().etd_batch_schedule(self._h, ctypes.byref(par), ctypes.byref(us[0]), ctypes.byref(us[1])),
+                  "etd_batch_schedule")
+        return {"schedule": "parallel" if par.value else "serial", "trial_us_per_step_serial": us[0].value,
+                "trial_us_per_step_parallel": us[1].value}
 
     def close(self):
         if getattr(self, "_h", None):

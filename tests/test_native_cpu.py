@@ -91,6 +91,7 @@ def test_batch_arguments_rejected_on_the_host(L):
     assert L.etd_batch_create(ctypes.byref(p), 2, N3, h, D2, 0.01, 2, None) == nat.ETD_ERR_INVALID_ARG
     assert L.etd_batch_run(None, None, 1, None) == nat.ETD_ERR_INVALID_ARG
     assert L.etd_batch_destroy(None) == nat.ETD_OK
+    assert L.etd_batch_schedule(None, None, None, None) == nat.ETD_ERR_INVALID_ARG
 
 
 def _opts(L, dtype=None, route=None):
