@@ -321,14 +321,30 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   L.block = dim3((unsigned)(P * k->tpp));
   L.smem = pass_smem_bytes(*k, P, two ? 2 : 1);
   L.kind = kind;
-  memcpy(L.args, &a, sizeof(a));
-  L.args_size = sizeof(a);
-  L.alg_bytes = fields_rw * (double)pl->unknowns * sizeof(T);
   // One kernel serves every axis of a given length, with different tile sizes, so the opt-in
   // limit is raised to the device maximum (not to this launch's size, which a later launch of the
   // same kernel could then undercut).
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+  // Weight tables of FP32 2D plans: kernels of axis lengths up to 1536 stage their tile's rows in shared
+  // memory before the dependency wait (in place of the zeta table, which the table epilogue does not
+  // read); a launch whose rows do not fit, or are not whole 16-byte chunks, gets no tables and evaluates
+  // the weights per mode. Longer axes read the tables from global memory.
+  if constexpr (sizeof(T) == 4) {
+    if (a.coef && two && k->min_blocks == 1 && k->N <= 1536) {
+      const int fpm = op == OP_S1 ? 2 : 1;
+      const size_t need = L.smem - (size_t)N * sizeof(float) + 16 + (size_t)N * 2 * P * fpm * sizeof(float);
+      if ((2 * P * fpm) % 4 == 0 && need <= (size_t)optin) {
+        a.coef_smem = 1;
+        L.smem = need;
+      } else {
+        a.coef = nullptr;
+      }
+    }
+  }
+  memcpy(L.args, &a, sizeof(a));
+  L.args_size = sizeof(a);
+  L.alg_bytes = fields_rw * (double)pl->unknowns * sizeof(T);
   if (L.smem > (size_t)optin) return fail(ETD_ERR_UNSUPPORTED, "tile needs %zu B of shared memory (max %d)", L.smem, optin);
   if (L.smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
@@ -895,8 +911,8 @@ void phi12_fp64(double z, double& p1, double& p2) {
   }
 }
 
-// Per-mode phi-function weights of a 2D FP32 plan whose y axis runs the split-radix kernels, computed in
-// FP64 from zeta = tau D (mu_x + mu_y) with the closed-form 1D rates (those of append_axis_tables) and
+// Per-mode phi-function weights of a 2D FP32 plan (FFT routes, both the default and the split-radix
+// kernels read them), computed in FP64 from zeta = tau D (mu_x + mu_y) with the closed-form 1D rates (those of append_axis_tables) and
 // rounded once to FP32; layouts as documented for PassArgs::coef (the exponentials e^{-z}, e^{-c2 z} are
 // products of the per-axis tables).
 etd_status upload_coef_tables(etd_plan_s* pl) {

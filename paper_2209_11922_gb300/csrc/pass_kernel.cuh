@@ -80,6 +80,8 @@ template <class T> struct PassArgs {
   // kernel), [y mode][x mode]: S1 float2 {c2 tau phi1(-c2 z), tau (phi1 - phi2/c2)(-z)}, S2 float
   // tau phi2(-z)/c2, RK1 float tau phi1(-z).
   const T* coef;
+  int coef_smem;    // 1: the kernel stages its tile's weights in shared memory before the dependency wait
+                    // (set by the host for the lengths that do, TABLES_STAGED)
 };
 
 // Asynchronous global -> shared copies (cp.async): every load of a tile is in flight at once and
@@ -99,6 +101,14 @@ template <> struct V2<double> { using type = double2; };
 
 // FP32 kernels whose transforms fit are held to 64 registers (two 512-thread CTAs per SM), so that
 // twice as many warps hide shared-memory and FMA latency; the others keep 128.
+template <class T, int N> constexpr int pass_min_blocks();
+// Kernels compiled with the table epilogue (per-mode weight tables of FP32 2D plans): the FP32 ones with
+// the full register budget.
+template <class T, int N> constexpr bool TABLES_ON() { return sizeof(T) == 4 && pass_min_blocks<T, N>() == 1; }
+// Of those, the lengths whose tile leaves room for the tile's rows of the tables in shared memory
+// (staged before the dependency wait; the host passes no tables where a launch cannot stage them);
+// longer axes read the tables from global memory.
+template <class T, int N> constexpr bool TABLES_STAGED() { return TABLES_ON<T, N>() && N <= 1536; }
 template <class T, int N> constexpr int pass_min_blocks() {
   return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48)) ? 2 : 1;
 }
@@ -134,10 +144,13 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
   C* b1 = b0 + A.P * LP;
   C* scr = b0 + (two ? 2 : 1) * A.P * LP;
-  // spectral passes (two buffers) also stage the transformed axis's zeta, e, ec tables (3 N values)
-  T* tz = reinterpret_cast<T*>(scr + A.P * (TPP > 32 ? TPP / 32 : 1));
-  T* te = tz + N;
+  // spectral passes (two buffers) also stage the transformed axis's e, ec, zeta tables (3 N values);
+  // a pass that stages its weight tables (A.coef_smem) leaves zeta out (the table epilogue does not
+  // read it) and puts the weights at the next 16-byte boundary instead
+  T* te = reinterpret_cast<T*>(scr + A.P * (TPP > 32 ? TPP / 32 : 1));
   T* tcs = te + N;
+  T* tz = tcs + N;
+  T* tco = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tz) + 15) & ~(uintptr_t)15);
   const int tid = threadIdx.x, NT = blockDim.x;
   const int P = A.P;
   const int p = tid / TPP, l = tid % TPP;
@@ -297,11 +310,21 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     const C* gtw = reinterpret_cast<const C*>(A.tw);
     for (int i = tid; i < L::TWN; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
   }
+  const bool coef_smem = TABLES_STAGED<T, N>() && two && A.coef;
   if (two) {
     for (int i = tid; i < N; i += NT) {
-      cp_async<sizeof(T)>(&tz[i], &A.zeta[A.axis][i]);
+      if (!coef_smem) cp_async<sizeof(T)>(&tz[i], &A.zeta[A.axis][i]);
       cp_async<sizeof(T)>(&te[i], &A.ex[A.axis][i]);
       cp_async<sizeof(T)>(&tcs[i], &A.ec[A.axis][i]);
+    }
+  }
+  if (coef_smem) {
+    // rows j < N of the tile's 2P x modes, fpm floats per mode, as 16-byte chunks
+    const int fpm = op == OP_S1 ? 2 : 1;
+    const int cpr = 2 * A.P * fpm / 4;
+    for (int i = tid; i < N * cpr; i += NT) {
+      const int j = i / cpr, c = i - j * cpr;
+      cp_async<16>(tco + (size_t)i * 4, A.coef + ((size_t)j * A.nx + x0) * fpm + 4 * c);
     }
   }
   griddep_wait();
@@ -416,7 +439,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   // factors), with every table load of a chunk of positions issued before the first use. Same
   // effect on the buffers as the epilogue above.
   // Compiled into the kernels with the full register budget only; the others evaluate the weights.
-  constexpr bool TABLES = sizeof(T) == 4 && pass_min_blocks<T, N>() == 1;
+  constexpr bool TABLES = TABLES_ON<T, N>();
   auto table_epilogue = [&](int kind, C* bpk) {
     if constexpr (TABLES) {
       constexpr int CNT = (N + TPP - 1) / TPP, CH = 4;
@@ -425,13 +448,24 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       for (int c0 = 0; c0 < CNT; c0 += CH) {
         float4 cf4[CH];
         float2 cf2[CH];
+        if constexpr (TABLES_STAGED<T, N>()) {   // staged: row j holds the tile's P mode pairs
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int j = l + (c0 + c) * TPP;
-          if (c0 + c < CNT && j < N) {
-            const size_t m = ((size_t)j * A.nx + col) / 2;
-            if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(A.coef)[m];
-            else cf2[c] = reinterpret_cast<const float2*>(A.coef)[m];
+          for (int c = 0; c < CH; ++c) {
+            const int j = l + (c0 + c) * TPP;
+            if (c0 + c < CNT && j < N) {
+              if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(tco)[j * P + p];
+              else cf2[c] = reinterpret_cast<const float2*>(tco)[j * P + p];
+            }
+          }
+        } else {           // the plan's [y mode][x mode] table
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const int j = l + (c0 + c) * TPP;
+            if (c0 + c < CNT && j < N) {
+              const size_t m = ((size_t)j * A.nx + col) / 2;
+              if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(A.coef)[m];
+              else cf2[c] = reinterpret_cast<const float2*>(A.coef)[m];
+            }
           }
         }
 #pragma unroll
