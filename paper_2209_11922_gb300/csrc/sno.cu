@@ -137,15 +137,17 @@ etd_status mma_launch(const MmaArgs& g, int num_sms, cudaStream_t s) {
     attr_set = true;
   }
   // CTAs per SM: at most 512 / NCOL (tensor-memory columns; a CTA that cannot allocate would wait for
-  // a co-resident one to finish), at most 16 (threads); the launch asks for enough shared memory that
-  // no more fit, and the grid covers that many per SM (CTAs loop over tiles)
-  const int per_sm = std::min(16, 512 / NCOL);
+  // a co-resident one to finish), at most 2048 / kMmaThreads (threads); where the columns are the
+  // tighter limit the launch asks for enough shared memory that no more CTAs fit. The grid covers
+  // that many per SM (CTAs loop over tiles).
+  const int by_threads = 2048 / kMmaThreads;
+  const int per_sm = std::min(by_threads, 512 / NCOL);
   const size_t floor_bytes = (size_t)228 * 1024 / (per_sm + 1) + 1024;
-  const size_t launch_smem = std::max(smem, per_sm < 16 ? floor_bytes : (size_t)0);
+  const size_t launch_smem = std::max(smem, per_sm < by_threads ? floor_bytes : (size_t)0);
   const long long tiles = (long long)g.tiles_per_img * g.imgs;
   const int fit = (int)std::min<size_t>(per_sm, (size_t)227 * 1024 / launch_smem);
   const int grid = (int)std::min<long long>(tiles, (long long)std::max(1, fit) * num_sms);
-  sno_mma_kernel<NCOL, EPI><<<grid, 128, launch_smem, s>>>(g);
+  sno_mma_kernel<NCOL, EPI><<<grid, kMmaThreads, launch_smem, s>>>(g);
   SNO_CUDA(cudaGetLastError());
   return ETD_OK;
 }

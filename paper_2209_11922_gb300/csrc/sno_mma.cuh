@@ -7,12 +7,12 @@
 // each as D[r][c] = sum_k A[r][k] B[c][k] over tiles of 128 rows r, with every output column c of the
 // contraction in one tile (c < NCOL <= 256) and the whole K (<= 256) resident.
 //
-// A CTA (4 warps) stages the constant operand B once, then loops over row tiles: all threads convert
+// A CTA (8 warps) stages the constant operand B once, then loops over row tiles: all threads convert
 // the tile's A rows from FP32 global memory to BF16 in shared memory (K-major, 64-byte rows, swizzled
 // as the tensor core reads them: 16-byte chunk q of row r at chunk position q ^ ((r / 2) % 4), 8-row
 // atoms of 512 bytes, one 128 x 32 block per 32 values of K), one thread issues the MMAs (K = 16 per
-// instruction) and commits them to an mbarrier, and each warp reads its 32 rows of the accumulator
-// from tensor memory for the fused epilogue. Waits are limited in time (umma::mbar_wait); a CTA that
+// instruction) and commits them to an mbarrier, and each warp reads 32 rows and half the columns of
+// the accumulator from tensor memory for the fused epilogue. Waits are limited in time (umma::mbar_wait); a CTA that
 // runs out sets the error word and stops.
 #pragma once
 #include <cuda_bf16.h>
@@ -60,28 +60,51 @@ __device__ __forceinline__ uint4 pack_bf16x8(const float (&v)[8]) {
 }
 
 // Stages R x kpad values M[r][k] = src[r rs + k ks] (0 outside r < rvalid, k < kvalid) as bf16 into
-// the swizzled K-major blocks at dst (block kc of R x 64 bytes holds k = 32 kc .. 32 kc + 31). A thread
-// converts 8 consecutive k of one row; threads walk the operand's contiguous index.
+// the swizzled K-major blocks at dst (block kc of R x 64 bytes holds k = 32 kc .. 32 kc + 31). An item
+// is 8 consecutive k of one row (one 16-byte chunk). K-contiguous sources (ks = 1): eight consecutive
+// items fill two adjacent rows of one block, so a warp's stores cover 512 contiguous bytes (no bank
+// conflicts) and its loads read 8 rows of 128 bytes. Other sources: consecutive items take consecutive
+// rows (coalesced loads along r). Each thread takes four items per round and issues all their loads
+// before converting any, to keep enough loads in flight.
 __device__ __forceinline__ void stage_bf16(unsigned char* dst, int R, const float* __restrict__ src, long long rs,
                                            long long ks, int rvalid, int kvalid, int kpad, int tid, int nt) {
-  const int q8 = kpad / 8;                 // 8-value chunks per row
+  constexpr int U = 4;
+  const int q8 = kpad / 8;   // items per row
+  const int total = R * q8;
   const bool kfast = ks == 1;
-  for (int it = tid; it < R * q8; it += nt) {
-    const int r = kfast ? it / q8 : it % R;
-    const int q = kfast ? it % q8 : it / R;
-    float v[8];
+  for (int base = tid; base < total; base += U * nt) {
+    float v[U][8];
+    int off[U];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int k = 8 * q + e;
-      v[e] = (r < rvalid && k < kvalid) ? src[(long long)r * rs + (long long)k * ks] : 0.f;
+    for (int u = 0; u < U; ++u) {
+      const int it = base + u * nt;
+      int r, q;
+      if (kfast) {
+        const int kc = it / (4 * R), rem = it - kc * 4 * R;
+        r = rem >> 2;
+        q = 4 * kc + (rem & 3);
+      } else {
+        q = it / R;
+        r = it - q * R;
+      }
+      const bool ok = it < total;
+      off[u] = ok ? (q >> 2) * R * 64 + r * 64 + (((q & 3) ^ ((r >> 1) & 3)) << 4) : -1;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = 8 * q + e;
+        v[u][e] = (ok && r < rvalid && k < kvalid) ? src[(long long)r * rs + (long long)k * ks] : 0.f;
+      }
     }
-    const int kc = q >> 2, c = q & 3;
-    *reinterpret_cast<uint4*>(dst + (size_t)kc * R * 64 + r * 64 + ((c ^ ((r >> 1) & 3)) << 4)) = pack_bf16x8(v);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (off[u] >= 0) *reinterpret_cast<uint4*>(dst + off[u]) = pack_bf16x8(v[u]);
   }
 }
 
+constexpr int kMmaThreads = 256;   // 8 warps: warps w and w + 4 read accumulator lanes 32 (w mod 4) ..
+
 template <int NCOL, int EPI>
-__global__ void __launch_bounds__(128) sno_mma_kernel(const MmaArgs g) {
+__global__ void __launch_bounds__(kMmaThreads) sno_mma_kernel(const MmaArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sA =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -98,20 +121,22 @@ __global__ void __launch_bounds__(128) sno_mma_kernel(const MmaArgs g) {
     umma::mbar_fence_init();
   }
   if (warp == 0) umma::tmem_alloc(tslot, NCOL < 32 ? 32 : NCOL);
-  stage_bf16(sB, NCOL, g.B, g.b_cs, g.b_ks, g.ncol, g.kvalid, g.kpad, tid, 128);
+  stage_bf16(sB, NCOL, g.B, g.b_cs, g.b_ks, g.ncol, g.kvalid, g.kpad, tid, kMmaThreads);
   umma::fence_proxy_async();
   umma::tc_fence_before();
   __syncthreads();
   umma::tc_fence_after();
   const uint32_t tmem = *tslot;
   constexpr uint32_t IDESC = umma::instr_desc(1u, 128, NCOL);   // BF16 x BF16 -> FP32, M = 128
+  constexpr int CW = NCOL / 2;                                   // accumulator columns per warp
+  const int lg = warp & 3, half = warp >> 2;
   const int ntiles = g.tiles_per_img * g.imgs;
   uint32_t phase = 0;
   bool ok = true;
   for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int img = t / g.tiles_per_img, r0 = (t % g.tiles_per_img) * 128;
     stage_bf16(sA, 128, g.A + (long long)img * g.a_is + (long long)r0 * g.a_rs, g.a_rs, g.a_ks, g.rows - r0,
-               g.kvalid, g.kpad, tid, 128);
+               g.kvalid, g.kpad, tid, kMmaThreads);
     umma::fence_proxy_async();
     umma::tc_fence_before();
     __syncthreads();
@@ -126,19 +151,41 @@ __global__ void __launch_bounds__(128) sno_mma_kernel(const MmaArgs g) {
         }
       umma::mma_commit(bar);
     }
+    // epilogue: warp w holds rows r0 + 32 (w mod 4) + lane (accumulator lanes 32 (w mod 4) ..) and
+    // columns [CW (w / 4), CW (w / 4 + 1)); the values the epilogue adds to are loaded before the wait
+    const int r = r0 + 32 * lg + lane;
+    const bool rv = r < g.rows;
+    float* C = g.C + (long long)img * g.c_is + (long long)r * g.c_rs;
+    float cpre[CW < 16 ? CW : 16];
+    if constexpr (EPI != ME_STORE && CW == 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = half * CW + i;
+        cpre[i] = (rv && c < g.ncol) ? C[(long long)c * g.c_cs] : 0.f;
+      }
+    }
     ok = __all_sync(0xffffffffu, umma::mbar_wait(bar, phase, abort_flag, g.err));
     phase ^= 1u;
     umma::tc_fence_after();
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!ok) break;
-    // epilogue: warp w holds rows r0 + 32 w + lane in TMEM lanes 32 w ..
-    const int r = r0 + 32 * warp + lane;
-    const bool rv = r < g.rows;
-    float* C = g.C + (long long)img * g.c_is + (long long)r * g.c_rs;
 #pragma unroll 1
-    for (int c0 = 0; c0 < NCOL; c0 += 16) {
+    for (int c0 = half * CW; c0 < (half + 1) * CW; c0 += 16) {
+      float cv[16];
+      if constexpr (EPI != ME_STORE) {
+        if constexpr (CW == 16) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) cv[i] = cpre[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int c = c0 + i;
+            cv[i] = (rv && c < g.ncol) ? C[(long long)c * g.c_cs] : 0.f;
+          }
+        }
+      }
       float v[16];
-      umma::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+      umma::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c0, v);
       if (!rv) continue;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -148,9 +195,9 @@ __global__ void __launch_bounds__(128) sno_mma_kernel(const MmaArgs g) {
         if constexpr (EPI == ME_STORE) {
           *p = v[i];
         } else if constexpr (EPI == ME_ACCUM) {
-          *p = v[i] + g.beta * *p;
+          *p = v[i] + g.beta * cv[i];
         } else {
-          const float z = v[i] + g.beta * *p + g.bias[c];
+          const float z = v[i] + g.beta * cv[i] + g.bias[c];
           *p = z;
           g.C2[(long long)img * g.c_is + (long long)r * g.c_rs + (long long)c * g.c_cs] = gelu(z);
         }
