@@ -505,13 +505,13 @@ def measure_sno(args, sw) -> dict:
     g = torch.empty_like(u0)
     ms_coarse = timed(lambda: sno.forward(u0, D, out=g, stream=stream), args.steps)
     fl = 2.0 * B * sw.C * sw.L * (2 * (n * n * sw.M + n * sw.M * sw.M) + sw.C * n * n)   # GEMM flops
-    # Algorithmic bytes of one forward (FP32 activations): lift (u in, h_0 out); per layer the mesh
-    # contraction of the truncated transform (h in, T out), its second contraction (T in, modes out),
-    # the mode mix (modes in and out), the first inverse contraction (modes in, T out), the second
-    # (T in, z out) and the pointwise mix with GELU (h and z in, z and h' out); projection (h_L, u in,
-    # u_hat out).
+    # Algorithmic bytes of one inference forward (FP32 activations): lift (u in, h_0 out); per layer the
+    # mesh contraction of the truncated transform (h in, T out), its second contraction (T in, modes
+    # out), the mode mix (modes in and out), the first inverse contraction (modes in, T out), the second
+    # (T in, z out) and the pointwise mix with GELU (h and z in, h' out); projection (h_L, u in, u_hat
+    # out).
     npix, C, M, L = n * n, sw.C, sw.M, sw.L
-    fwd_bytes = 4.0 * B * (npix + C * npix + L * (6 * C * npix + 4 * C * M * n + 4 * C * M * M) + C * npix + 2 * npix)
+    fwd_bytes = 4.0 * B * (npix + C * npix + L * (5 * C * npix + 4 * C * M * n + 4 * C * M * M) + C * npix + 2 * npix)
     hbm_peak, hbm_src = _peaks()
     achieved = fwd_bytes / (ms_coarse * 1e-3) / 1e9
     line = {

@@ -165,6 +165,10 @@ etd_status mma_run(const MmaArgs& g, int num_sms, cudaStream_t s) {
     if (st_ != ETD_OK) return st_;     \
   } while (0)
 
+// The dedicated kernel of the second truncated-transform contraction holds both M x n operands in
+// shared memory.
+bool small_modes(const etd_sno_s* m) { return m->M <= 32 && 2 * (size_t)m->M * m->n * sizeof(float) <= 227 * 1024; }
+
 // out (M x M per image) = S_M X S_M^T for `imgs` images X (n x n); T is scratch (n x M per image).
 // round: bf16-round the result. tc: the first contraction (X S_M^T, K = n) on the tensor cores with
 // bf16 X and S_M, T then stored [M][n] per image.
@@ -185,6 +189,17 @@ etd_status modes_of(const etd_sno_s* m, const float* X, int imgs, float* out, bo
     g.err = m->err;
     SNO_TRY(mma_run<ME_STORE>(g, m->num_sms, s));
     // out = S_M T^T  (M x M)
+    if (small_modes(m)) {
+      const size_t smem = 2 * (size_t)M * n * sizeof(float);
+      static bool attr_set = false;
+      if (!attr_set) {
+        SNO_CUDA(cudaFuncSetAttribute(modes_pm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_set = true;
+      }
+      modes_pm_kernel<<<imgs, 64, smem, s>>>(m->S, m->T, out, n, M, round ? 1 : 0);
+      SNO_CUDA(cudaGetLastError());
+      return ETD_OK;
+    }
     GemmOp o(M, M, n, imgs);
     o.A(m->S, n, 1, 0).B(m->T, 1, n, (long long)M * n).Cm(out, M, 1, (long long)M * M);
     o.g.round_c = round ? 1 : 0;
@@ -204,7 +219,12 @@ etd_status modes_of(const etd_sno_s* m, const float* X, int imgs, float* out, bo
 etd_status field_of(const etd_sno_s* m, const float* Y, int imgs, float* out, float beta, bool tc, cudaStream_t s) {
   const int n = m->n, M = m->M;
   // T = Y S_M  (M x n)
-  SNO_TRY(GemmOp(M, n, M, imgs).A(Y, M, 1, (long long)M * M).B(m->S, n, 1, 0).Cm(m->T, n, 1, (long long)M * n).run(s));
+  if (M <= 32) {
+    modes_to_rows_kernel<<<imgs, 256, 0, s>>>(Y, m->S, m->T, n, M);
+    SNO_CUDA(cudaGetLastError());
+  } else {
+    SNO_TRY(GemmOp(M, n, M, imgs).A(Y, M, 1, (long long)M * M).B(m->S, n, 1, 0).Cm(m->T, n, 1, (long long)M * n).run(s));
+  }
   if (tc) {
     // out[i][j] = sum_m S_M[m][i] T[m][j], as D[j][i] over tiles of 128 j
     MmaArgs g;
@@ -274,8 +294,9 @@ etd_status check_err(etd_sno_s* m) {
   return ETD_OK;
 }
 
-// Forward pass for B fields; keeps h, z, hh for the gradient.
-etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStream_t s) {
+// Forward pass for B fields; with `keep` it also keeps h, z, hh for the gradient (without, the
+// pre-activations z are not stored: inference).
+etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStream_t s, bool keep) {
   const int C = m->C, M = m->M, L = m->L;
   const long long np = m->npix, img = (long long)C * np, M2 = (long long)M * M;
   lift_kernel<<<dim3(grid_for(np) < 64 ? grid_for(np) : 64, B * C), 256, 0, s>>>(u, m->a, m->W + m->oWl,
@@ -309,7 +330,7 @@ etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStre
       g.bias = m->W + m->obp + (long long)l * C;
       g.C2 = m->h[l + 1];
       g.err = m->err;
-      SNO_TRY(mma_run<ME_PW_GELU>(g, m->num_sms, s));
+      SNO_TRY(keep ? mma_run<ME_PW_GELU>(g, m->num_sms, s) : mma_run<ME_PW_GELU_ONLY>(g, m->num_sms, s));
     } else {
       GemmOp o(C, (int)np, C, B);
       o.A(m->W + m->oWp + (long long)l * C * C, C, 1, 0).B(m->h[l], np, 1, img).Cm(m->z[l], np, 1, img);
@@ -321,12 +342,10 @@ etd_status sno_forward(etd_sno_s* m, const float* u, int B, float* out, cudaStre
     }
   }
   // out[b] = u[b] + Wq . h_L[b] + bq
-  GemmOp o(1, (int)np, C, B);
-  o.A(m->W + m->oWq, C, 1, 0).B(m->h[L], np, 1, img).Cm(out, np, 1, np);
-  o.g.epi = SG_RESID;
-  o.g.R = u;
-  o.g.bias = m->W + m->obq;
-  return o.run(s);
+  const int pblk = (int)std::min<long long>((np + 255) / 256, 64);
+  project_kernel<<<dim3(pblk, B), 256, 0, s>>>(u, m->h[L], m->W + m->oWq, m->W + m->obq, out, C, np);
+  SNO_CUDA(cudaGetLastError());
+  return ETD_OK;
 }
 
 // sum over fields and pixels of X[b][c][i] * (y ? y[b][i] : 1), weighted per field by w (device,
@@ -506,7 +525,7 @@ etd_status etd_sno_forward(etd_sno m, const float* u, const double* D, int B, fl
   if (out == u) return sfail(ETD_ERR_INVALID_ARG, "out may not alias u");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SNO_TRY(upload_feature(m, D, B, s));
-  return sno_forward(m, u, B, out, s);
+  return sno_forward(m, u, B, out, s, false);
 }
 
 etd_status etd_sno_train_step(etd_sno m, const float* u, const double* D, const float* target, int B, float lr,
@@ -516,7 +535,7 @@ etd_status etd_sno_train_step(etd_sno m, const float* u, const double* D, const 
   if (!(std::isfinite(lr) && lr >= 0)) return sfail(ETD_ERR_INVALID_ARG, "lr must be finite and >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SNO_TRY(upload_feature(m, D, B, s));
-  SNO_TRY(sno_forward(m, u, B, m->uhat, s));
+  SNO_TRY(sno_forward(m, u, B, m->uhat, s, true));
   const long long n = (long long)B * m->npix;
   mse_grad_kernel<<<m->lblocks, 256, 0, s>>>(m->uhat, target, m->du, n, m->lpart);
   SNO_CUDA(cudaGetLastError());

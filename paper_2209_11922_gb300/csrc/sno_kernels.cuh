@@ -150,6 +150,99 @@ __global__ void lift_kernel(const float* __restrict__ u, const float* __restrict
     hb[i] = w0 * ub[i] + off;
 }
 
+// Second contraction of the truncated transform, per image: out[p][m] = sum_i S[p][i] T[m][i] for
+// p, m < M <= 32, i < n (S: the M x n mode matrix S_M; T: the first contraction's [m][i] rows), rounded
+// to bf16 when `round`. One CTA of 64 threads per image: both operands' rows in shared memory with the
+// odd stride n (distinct banks for the 8 rows a warp reads at one i), each thread a 4 x 4 block of
+// outputs (p = tp + 8a, m = tm + 8b) accumulated in FP32 over i in order.
+__global__ void __launch_bounds__(64) modes_pm_kernel(const float* __restrict__ S, const float* __restrict__ T,
+                                                      float* __restrict__ out, int n, int M, int round) {
+  extern __shared__ float sm[];
+  float* Ss = sm;
+  float* Ts = sm + (size_t)M * n;
+  const int img = blockIdx.x, tid = threadIdx.x;
+  const float* Ti = T + (size_t)img * M * n;
+  for (int e = tid; e < M * n; e += 64) {
+    Ss[e] = S[e];
+    Ts[e] = Ti[e];
+  }
+  __syncthreads();
+  const int tp = tid & 7, tm = tid >> 3;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  int pr[4], mr[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    pr[a] = min(tp + 8 * a, M - 1) * n;   // clamped rows: computed, not stored
+    mr[a] = min(tm + 8 * a, M - 1) * n;
+  }
+  for (int i = 0; i < n; ++i) {
+    float sv[4], tv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      sv[a] = Ss[pr[a] + i];
+      tv[a] = Ts[mr[a] + i];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(sv[a], tv[b], acc[a][b]);
+  }
+  float* o = out + (size_t)img * M * M;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int pp = tp + 8 * a, mm = tm + 8 * b;
+      if (pp < M && mm < M) o[pp * M + mm] = round ? bf16_round(acc[a][b]) : acc[a][b];
+    }
+}
+
+// First contraction of the inverse truncated transform, per image: T[m][j] = sum_q Y[m][q] S[q][j] for
+// m < M <= 32, j < n (Y: the M x M modes; S: S_M). One CTA per image, one output column j per thread
+// (coalesced loads of S and stores of T), Y in shared memory read as broadcasts, FP32 accumulation
+// over q in order.
+__global__ void __launch_bounds__(256) modes_to_rows_kernel(const float* __restrict__ Y, const float* __restrict__ S,
+                                                            float* __restrict__ T, int n, int M) {
+  __shared__ float Ys[32 * 32];
+  const int img = blockIdx.x;
+  const float* Yi = Y + (size_t)img * M * M;
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) Ys[e] = Yi[e];
+  __syncthreads();
+  float* Ti = T + (size_t)img * M * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float acc[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) acc[m] = 0.f;
+    for (int q = 0; q < M; ++q) {
+      const float s = S[(size_t)q * n + j];
+#pragma unroll
+      for (int m = 0; m < 32; ++m)
+        if (m < M) acc[m] = fmaf(Ys[m * M + q], s, acc[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < 32; ++m)
+      if (m < M) Ti[(size_t)m * n + j] = acc[m];
+  }
+}
+
+// Projection onto the increment: out[b][i] = u[b][i] + bq + sum_c Wq[c] h[b][c][i] (FP32, channels in
+// order); grid (pixel blocks, B).
+__global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ u, const float* __restrict__ h,
+                                                      const float* __restrict__ Wq, const float* __restrict__ bq,
+                                                      float* __restrict__ out, int C, long long npix) {
+  const int b = blockIdx.y;
+  const float* hb = h + (size_t)b * C * npix;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int c = 0; c < C; ++c) acc = fmaf(Wq[c], hb[(size_t)c * npix + i], acc);
+    out[(size_t)b * npix + i] = acc + (u[(size_t)b * npix + i] + bq[0]);
+  }
+}
+
 // dz = dh * gelu'(z)
 __global__ void gelu_backward_kernel(const float* __restrict__ dh, const float* __restrict__ z, float* __restrict__ dz,
                                      long long n) {

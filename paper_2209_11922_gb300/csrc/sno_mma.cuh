@@ -3,7 +3,7 @@
 //   T1  the truncated sine transform along x, T[img][m][i] = sum_j bf(X[img][i][j]) bf(S_M[m][j]),
 //   F2  the inverse truncated transform along y, out[img][i][j] (+)= sum_m bf(S_M[m][i]) bf(T[img][m][j]),
 //   PW  the pointwise channel mix of a layer, z[b][o][i] = sum_c bf(Wp[o][c]) bf(h[b][c][i]) + z + bp[o],
-//       h'[b][o][i] = gelu(z),
+//       h'[b][o][i] = gelu(z) (ME_PW_GELU stores z too, for the gradient; ME_PW_GELU_ONLY only h'),
 // each as D[r][c] = sum_k A[r][k] B[c][k] over tiles of 128 rows r, with every output column c of the
 // contraction in one tile (c < NCOL <= 256) and the whole K (<= 256) resident.
 //
@@ -25,7 +25,7 @@
 namespace etd {
 namespace sno {
 
-enum MmaEpi : int { ME_STORE = 0, ME_ACCUM = 1, ME_PW_GELU = 2 };
+enum MmaEpi : int { ME_STORE = 0, ME_ACCUM = 1, ME_PW_GELU = 2, ME_PW_GELU_ONLY = 3 };
 
 struct MmaArgs {
   int tiles_per_img, imgs;       // tile t: image t / tiles_per_img, rows r0 = 128 (t % tiles_per_img)
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kMmaThreads) sno_mma_kernel(const MmaArgs g) {
           *p = v[i] + g.beta * cv[i];
         } else {
           const float z = v[i] + g.beta * cv[i] + g.bias[c];
-          *p = z;
+          if constexpr (EPI == ME_PW_GELU) *p = z;
           g.C2[(long long)img * g.c_is + (long long)r * g.c_rs + (long long)c * g.c_cs] = gelu(z);
         }
       }
