@@ -45,27 +45,36 @@ def test_batch_equals_one_plan_per_problem(dtype, scheme):
         assert rel <= tol, (i, PROBLEMS[i], rel)
 
 
-def test_batch_schedules_give_identical_fields():
-    """The serial and the parallel-branch schedules run the same kernels on disjoint problems, so the
-    fields agree bit for bit; the creation-time choice reports both trial times."""
+def test_batch_schedules_give_identical_fields(monkeypatch):
+    """The serial and the parallel-branch schedules run the same kernels on disjoint problems, so with the
+    same tile sizes (the fixed choice, autotuning off) the fields agree bit for bit; the creation-time
+    choice (autotuned tiles, both schedules timed) reports both trial times and keeps the faster, and its
+    fields agree with the others to the FP32 bound (autotuned tiles may differ: results depend on the
+    tile size at rounding level, see the design notes)."""
     from paper_2209_11922_gb300.etd import Batch
     tau, nsteps = 1e-2, 70     # two 32-step graph replays and 6 direct steps
     out = {}
     for sched in ("serial", "parallel", "auto"):
-        f = _fields(PROBLEMS, "f32", seed0=700)
-        with Batch([p[0] for p in PROBLEMS], [p[1] for p in PROBLEMS], tau, 2, "f32", schedule=sched) as b:
-            b.run(f, nsteps)
-            out[sched] = (f, b.schedule())
+        with monkeypatch.context() as mp:
+            if sched != "auto":
+                mp.setenv("ETD_AUTOTUNE", "0")
+            f = _fields(PROBLEMS, "f32", seed0=700)
+            with Batch([p[0] for p in PROBLEMS], [p[1] for p in PROBLEMS], tau, 2, "f32", schedule=sched) as b:
+                b.run(f, nsteps)
+                out[sched] = (f, b.schedule(), b.info()["tile_pairs"])
     torch.cuda.synchronize()
     assert out["serial"][1]["schedule"] == "serial" and out["parallel"][1]["schedule"] == "parallel"
+    assert out["serial"][2] == out["parallel"][2]
+    for i, (a, b) in enumerate(zip(out["serial"][0], out["parallel"][0])):
+        assert torch.equal(a, b), (i, PROBLEMS[i])
     auto = out["auto"][1]
     print(f"schedule trial: {auto}")
     assert auto["trial_us_per_step_serial"] > 0 and auto["trial_us_per_step_parallel"] > 0
     faster = "parallel" if auto["trial_us_per_step_parallel"] < auto["trial_us_per_step_serial"] else "serial"
     assert auto["schedule"] == faster
-    for sched in ("parallel", "auto"):
-        for i, (a, b) in enumerate(zip(out["serial"][0], out[sched][0])):
-            assert torch.equal(a, b), (sched, i, PROBLEMS[i])
+    for i, (a, b) in enumerate(zip(out["serial"][0], out["auto"][0])):
+        rel = float((a.double() - b.double()).norm() / b.double().norm())
+        assert rel <= 1e-5, (i, PROBLEMS[i], rel)
 
 
 def test_batch_matches_oracle():
