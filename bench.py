@@ -390,6 +390,35 @@ def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
     for pl in plans:
         pl.close()
     batch.close()
+    # Transform route per length: one N x N plan per distinct length of the batch on each route (the
+    # tensor-core routes need N % 32 == 0), microseconds per time step and the route's rel L2 difference
+    # from the FFT route after the same steps: what an FFT-versus-GEMM choice per length would pick from.
+    per_len = {}
+    if dtype == "f32":
+        lengths = sorted({n for (nx, ny), _ in probs for n in (nx, ny)})
+        for n in lengths:
+            row, ref_u = {}, None
+            u0 = torch.from_numpy(bw.u0(0, (n - 1, n - 1)).astype(np.float32)).cuda()
+            for route in ("auto", "gemm_tf32", "gemm_bf16x3"):
+                if route != "auto" and n % 32:
+                    continue
+                with Plan((n, n), 3e-3, bw.tau, 2, "f32", route=route) as pl:
+                    u = u0.clone()
+                    pl.run(u, 64, stream)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    pl.run(u, 256, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    row[route] = {"us_per_step": e0.elapsed_time(e1) * 1e3 / 256}
+                    v = u0.clone()
+                    pl.run(v, 20, stream)
+                    if route == "auto":
+                        ref_u = v.double()
+                    else:
+                        row[route]["rel_l2_vs_fft_20_steps"] = float((v.double() - ref_u).norm() / ref_u.norm())
+            per_len[str(n)] = row
     esz = 4 if dtype == "f32" else 8
     achieved = 11 * unknowns * esz / (ms / steps / nsteps * 1e-3) / 1e9
     peak, peak_src = _peaks()
@@ -397,7 +426,7 @@ def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
             "value": value, "unit": UNIT, "ms_per_run": ms / steps, "plans_value": value_plans,
             "speedup_vs_plans": value / value_plans, "launches_per_time_step": info["launches_per_step"],
             "tuned_tile_pairs": info["tile_pairs"], "schedule": sched, "create_s": round(create_s, 3),
-            "runs_timed": steps,
+            "route_per_length": per_len, "runs_timed": steps,
             "gpu_launches": steps * (info["launches_per_step"] * nsteps + 12),
             "roofline": {"bound": "hbm", "kernel": "one time step (all grouped launches)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
@@ -422,7 +451,8 @@ def run_batched(args, bw):
                    "schedule": m["schedule"], "create_s": m["create_s"],
                    "l2": "256 MiB buffer written between bench steps"},
         "gpu_launches": m["gpu_launches"], "plans_value": m["plans_value"],
-        "speedup_vs_plans": m["speedup_vs_plans"], "roofline": m["roofline"], "clocks": clk.summary(),
+        "speedup_vs_plans": m["speedup_vs_plans"], "route_per_length": m["route_per_length"],
+        "roofline": m["roofline"], "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0
