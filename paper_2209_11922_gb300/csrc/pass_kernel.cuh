@@ -312,10 +312,16 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   }
   const bool coef_smem = TABLES_STAGED<T, N>() && two && A.coef;
   if (two) {
+    // the transformed axis's tables, selected without indexing the descriptor's arrays by a run-time
+    // value (which would keep a batched kernel's copy of the descriptor in local memory)
+    const int ax = A.axis;
+    const T* gz = ax == 0 ? A.zeta[0] : (ax == 1 ? A.zeta[1] : A.zeta[2]);
+    const T* ge = ax == 0 ? A.ex[0] : (ax == 1 ? A.ex[1] : A.ex[2]);
+    const T* gc = ax == 0 ? A.ec[0] : (ax == 1 ? A.ec[1] : A.ec[2]);
     for (int i = tid; i < N; i += NT) {
-      if (!coef_smem) cp_async<sizeof(T)>(&tz[i], &A.zeta[A.axis][i]);
-      cp_async<sizeof(T)>(&te[i], &A.ex[A.axis][i]);
-      cp_async<sizeof(T)>(&tcs[i], &A.ec[A.axis][i]);
+      if (!coef_smem) cp_async<sizeof(T)>(&tz[i], &gz[i]);
+      cp_async<sizeof(T)>(&te[i], &ge[i]);
+      cp_async<sizeof(T)>(&tcs[i], &gc[i]);
     }
   }
   if (coef_smem) {
@@ -596,8 +602,9 @@ template <class T, int N, int VAR, int OPC>
 __global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
     pass_kernel_batched_op(const PassArgs<T>* __restrict__ descs, const int2* __restrict__ map, T* const* __restrict__) {
   const int2 m = map[blockIdx.x];
-  PassArgs<T> A = descs[m.x];
-  pass_body<T, N, VAR, OPC>(A, m.y);
+  // the descriptor is read in place (read-only global memory, reloaded where needed) rather than copied
+  // into registers, which the stage passes cannot spare
+  pass_body<T, N, VAR, OPC>(descs[m.x], m.y);
 }
 
 // Host-side description of one instantiation.
