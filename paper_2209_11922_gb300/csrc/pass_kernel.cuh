@@ -325,12 +325,13 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     }
   }
   if (coef_smem) {
-    // rows j < N of the tile's 2P x modes, fpm floats per mode, as 16-byte chunks
+    // rows j < N of the tile's 2P x modes, fpm floats per mode, as 16-byte chunks stored chunk-major
+    // ([chunk c][row j]: the lanes of a warp, consecutive j, then read consecutive chunks)
     const int fpm = op == OP_S1 ? 2 : 1;
     const int cpr = 2 * A.P * fpm / 4;
     for (int i = tid; i < N * cpr; i += NT) {
       const int j = i / cpr, c = i - j * cpr;
-      cp_async<16>(tco + (size_t)i * 4, A.coef + ((size_t)j * A.nx + x0) * fpm + 4 * c);
+      cp_async<16>(tco + ((size_t)c * N + j) * 4, A.coef + ((size_t)j * A.nx + x0) * fpm + 4 * c);
     }
   }
   griddep_wait();
@@ -454,13 +455,13 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       for (int c0 = 0; c0 < CNT; c0 += CH) {
         float4 cf4[CH];
         float2 cf2[CH];
-        if constexpr (TABLES_STAGED<T, N>()) {   // staged: row j holds the tile's P mode pairs
+        if constexpr (TABLES_STAGED<T, N>()) {   // staged chunk-major: S1 one pair per chunk, else two
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
             const int j = l + (c0 + c) * TPP;
             if (c0 + c < CNT && j < N) {
-              if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(tco)[j * P + p];
-              else cf2[c] = reinterpret_cast<const float2*>(tco)[j * P + p];
+              if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(tco)[p * N + j];
+              else cf2[c] = reinterpret_cast<const float2*>(tco)[((p >> 1) * N + j) * 2 + (p & 1)];
             }
           }
         } else {           // the plan's [y mode][x mode] table
