@@ -20,6 +20,11 @@ __device__ __forceinline__ float bf16_round(float x) {
   b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
   return __uint_as_float(b);
 }
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
@@ -146,8 +151,16 @@ __global__ void lift_kernel(const float* __restrict__ u, const float* __restrict
   const float w0 = Wl[2 * c], off = Wl[2 * c + 1] * a[b] + bl[c];
   const float* ub = u + (long long)b * npix;
   float* hb = h + (long long)bc * npix;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x)
-    hb[i] = w0 * ub[i] + off;
+  // four elements per thread and round (coalesced: the four are blockDim apart), loads before stores
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < npix; i0 += 4 * step) {
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = i0 + k * step < npix ? ub[i0 + k * step] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k * step < npix) hb[i0 + k * step] = w0 * v[k] + off;
+  }
 }
 
 // Second contraction of the truncated transform, per image: out[p][m] = sum_i S[p][i] T[m][i] for
@@ -157,14 +170,25 @@ __global__ void lift_kernel(const float* __restrict__ u, const float* __restrict
 // outputs (p = tp + 8a, m = tm + 8b) accumulated in FP32 over i in order.
 __global__ void __launch_bounds__(64) modes_pm_kernel(const float* __restrict__ S, const float* __restrict__ T,
                                                       float* __restrict__ out, int n, int M, int round) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   float* Ss = sm;
   float* Ts = sm + (size_t)M * n;
   const int img = blockIdx.x, tid = threadIdx.x;
   const float* Ti = T + (size_t)img * M * n;
-  for (int e = tid; e < M * n; e += 64) {
-    Ss[e] = S[e];
-    Ts[e] = Ti[e];
+  // both operands as asynchronous 16-byte copies, all in flight at once (M n is a multiple of 4 and
+  // both sources 16-byte aligned when M n is; otherwise element copies)
+  const int cnt = M * n;
+  if ((cnt & 3) == 0 && ((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(Ti)) & 15) == 0) {
+    for (int e = 4 * tid; e < cnt; e += 4 * 64) {
+      cp_async16(Ss + e, S + e);
+      cp_async16(Ts + e, Ti + e);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else {
+    for (int e = tid; e < cnt; e += 64) {
+      Ss[e] = S[e];
+      Ts[e] = Ti[e];
+    }
   }
   __syncthreads();
   const int tp = tid & 7, tm = tid >> 3;
@@ -205,8 +229,8 @@ __global__ void __launch_bounds__(64) modes_pm_kernel(const float* __restrict__ 
 // m < M <= 32, j < n (Y: the M x M modes; S: S_M). One CTA per image, one output column j per thread
 // (coalesced loads of S and stores of T), Y in shared memory read as broadcasts, FP32 accumulation
 // over q in order.
-__global__ void __launch_bounds__(256) modes_to_rows_kernel(const float* __restrict__ Y, const float* __restrict__ S,
-                                                            float* __restrict__ T, int n, int M) {
+__global__ void __launch_bounds__(256, 2) modes_to_rows_kernel(const float* __restrict__ Y, const float* __restrict__ S,
+                                                               float* __restrict__ T, int n, int M) {
   __shared__ float Ys[32 * 32];
   const int img = blockIdx.x;
   const float* Yi = Y + (size_t)img * M * M;
@@ -214,14 +238,30 @@ __global__ void __launch_bounds__(256) modes_to_rows_kernel(const float* __restr
   __syncthreads();
   float* Ti = T + (size_t)img * M * n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    // the thread's column of S_M in blocks of 8 values, the next block's loads in flight while the current
+    // one is used
     float acc[32];
 #pragma unroll
     for (int m = 0; m < 32; ++m) acc[m] = 0.f;
-    for (int q = 0; q < M; ++q) {
-      const float s = S[(size_t)q * n + j];
+    float sv[8], sn[8];
 #pragma unroll
-      for (int m = 0; m < 32; ++m)
-        if (m < M) acc[m] = fmaf(Ys[m * M + q], s, acc[m]);
+    for (int k = 0; k < 8; ++k) sv[k] = k < M ? S[(size_t)k * n + j] : 0.f;
+    for (int q0 = 0; q0 < M; q0 += 8) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int q = q0 + 8 + k;
+        sn[k] = q < M ? S[(size_t)q * n + j] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (q0 + k < M) {
+#pragma unroll
+          for (int m = 0; m < 32; ++m)
+            if (m < M) acc[m] = fmaf(Ys[m * M + q0 + k], sv[k], acc[m]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sv[k] = sn[k];
     }
 #pragma unroll
     for (int m = 0; m < 32; ++m)
