@@ -101,16 +101,18 @@ template <> struct V2<double> { using type = double2; };
 
 // FP32 kernels whose transforms fit are held to 64 registers (two 512-thread CTAs per SM), so that
 // twice as many warps hide shared-memory and FMA latency; the others keep 128.
-template <class T, int N> constexpr int pass_min_blocks();
+template <class T, int N, int VAR> constexpr int pass_min_blocks();
 // Kernels compiled with the table epilogue (per-mode weight tables of FP32 2D plans): the FP32 ones with
 // the full register budget.
-template <class T, int N> constexpr bool TABLES_ON() { return sizeof(T) == 4 && pass_min_blocks<T, N>() == 1; }
+template <class T, int N, int VAR> constexpr bool TABLES_ON() { return sizeof(T) == 4 && pass_min_blocks<T, N, VAR>() == 1; }
 // Of those, the lengths whose tile leaves room for the tile's rows of the tables in shared memory
 // (staged before the dependency wait; the host passes no tables where a launch cannot stage them);
 // longer axes read the tables from global memory.
-template <class T, int N> constexpr bool TABLES_STAGED() { return TABLES_ON<T, N>() && N <= 1536; }
-template <class T, int N> constexpr int pass_min_blocks() {
-  return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48)) ? 2 : 1;
+template <class T, int N, int VAR> constexpr bool TABLES_STAGED() { return TABLES_ON<T, N, VAR>() && N <= 1536; }
+template <class T, int N, int VAR> constexpr int pass_min_blocks() {
+  // 3 x 2^k lengths above 48 keep 128 registers (their radix-3/12 stages spill at 64), except the
+  // recurrence plan of N = 96 (radices 4, 3, 8), which fits
+  return (sizeof(T) == 4 && N <= 512 && (N % 3 != 0 || N <= 48 || (N == 96 && VAR == V_REC))) ? 2 : 1;
 }
 // The last pass of a time step counts it, in CTA 0, after the dependency wait (the step's reaction
 // passes, which read the count, have completed then). CTAs that return early (boundary tiles) call
@@ -310,7 +312,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     const C* gtw = reinterpret_cast<const C*>(A.tw);
     for (int i = tid; i < L::TWN; i += NT) cp_async<2 * sizeof(T)>(&tws[i], &gtw[i]);
   }
-  const bool coef_smem = TABLES_STAGED<T, N>() && two && A.coef;
+  const bool coef_smem = TABLES_STAGED<T, N, VAR>() && two && A.coef;
   if (two) {
     // the transformed axis's tables, selected without indexing the descriptor's arrays by a run-time
     // value (which would keep a batched kernel's copy of the descriptor in local memory)
@@ -446,7 +448,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   // factors), with every table load of a chunk of positions issued before the first use. Same
   // effect on the buffers as the epilogue above.
   // Compiled into the kernels with the full register budget only; the others evaluate the weights.
-  constexpr bool TABLES = TABLES_ON<T, N>();
+  constexpr bool TABLES = TABLES_ON<T, N, VAR>();
   auto table_epilogue = [&](int kind, C* bpk) {
     if constexpr (TABLES) {
       constexpr int CNT = (N + TPP - 1) / TPP, CH = 4;
@@ -455,7 +457,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       for (int c0 = 0; c0 < CNT; c0 += CH) {
         float4 cf4[CH];
         float2 cf2[CH];
-        if constexpr (TABLES_STAGED<T, N>()) {   // staged chunk-major: S1 one pair per chunk, else two
+        if constexpr (TABLES_STAGED<T, N, VAR>()) {   // staged chunk-major: S1 one pair per chunk, else two
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
             const int j = l + (c0 + c) * TPP;
@@ -506,7 +508,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   // two forward transforms of RK1/S1 (of U and of N0) together, sharing each Stockham pass's
   // barriers; under the halved budget the second set of butterfly registers would spill.
   int s0 = 0;
-  if constexpr (L::ODD && pass_min_blocks<T, N>() == 1) {
+  if constexpr (L::ODD && pass_min_blocks<T, N, VAR>() == 1) {
     if (op == OP_RK1 || op == OP_S1) {
       C* const bps[2] = {b0p, b1p};
       C* const scrs[2] = {scrp, scrp};   // unused by the odd-extension variant
@@ -564,13 +566,13 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
 
 // One plan: the launch covers the tiles of one field.
 template <class T, int N, int VAR>
-__global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel(const PassArgs<T> A) {
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N, VAR>()) pass_kernel(const PassArgs<T> A) {
   pass_body<T, N, VAR>(A, (int)blockIdx.x);
 }
 
 // The same with the operation fixed (A.op must equal OPC).
 template <class T, int N, int VAR, int OPC>
-__global__ void __launch_bounds__(512, pass_min_blocks<T, N>()) pass_kernel_op(const PassArgs<T> A) {
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N, VAR>()) pass_kernel_op(const PassArgs<T> A) {
   pass_body<T, N, VAR, OPC>(A, (int)blockIdx.x);
 }
 
@@ -587,7 +589,7 @@ template <class T, int N, int VAR> constexpr bool pass_op_kernels() {
 // length N. CTA b works on tile map[b].y of the problem described by descs[map[b].x]; entry and exit
 // passes take the caller's field pointer from user[descs[.].user_slot].
 template <class T, int N, int VAR>
-__global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N, VAR>())
     pass_kernel_batched(const PassArgs<T>* __restrict__ descs, const int2* __restrict__ map, T* const* __restrict__ user) {
   const int2 m = map[blockIdx.x];
   PassArgs<T> A = descs[m.x];
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
 
 // The same with the operation fixed (every descriptor's op must equal OPC).
 template <class T, int N, int VAR, int OPC>
-__global__ void __launch_bounds__(512, pass_min_blocks<T, N>())
+__global__ void __launch_bounds__(512, pass_min_blocks<T, N, VAR>())
     pass_kernel_batched_op(const PassArgs<T>* __restrict__ descs, const int2* __restrict__ map, T* const* __restrict__) {
   const int2 m = map[blockIdx.x];
   // the descriptor is read in place (read-only global memory, reloaded where needed) rather than copied
@@ -638,7 +640,7 @@ template <class T, int N, int VAR> KernelInfo kernel_info() {
                {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                N, L::TPP, L::LP, (int)sizeof(T), L::M,
-               VAR, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N>()};
+               VAR, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N, VAR>()};
   if constexpr (pass_op_kernels<T, N, VAR>()) {
     k.fn_op[OP_REACT] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_REACT>);
     k.fn_op[OP_TRANSFORM] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_TRANSFORM>);
