@@ -220,7 +220,7 @@ ETD_PLAN(float, 12, false, 2, 4, 3)
 ETD_PLAN(float, 24, false, 4, 8, 3)
 ETD_PLAN(float, 48, false, 4, 12, 4)
 ETD_PLAN(float, 96, false, 16, 4, 3, 8)
-ETD_PLAN(float, 192, false, 16, 12, 16)
+ETD_PLAN(float, 192, false, 16, 16, 12)
 ETD_PLAN(float, 384, false, 32, 8, 3, 16)
 ETD_PLAN(float, 768, false, 64, 16, 3, 16)
 ETD_PLAN(float, 1536, false, 128, 16, 6, 16)
