@@ -103,8 +103,11 @@ __device__ __forceinline__ void stage_bf16(unsigned char* dst, int R, const floa
 
 constexpr int kMmaThreads = 256;   // 8 warps: warps w and w + 4 read accumulator lanes 32 (w mod 4) ..
 
+// Narrow tiles (NCOL <= 64: the pointwise mix and the truncated transform) are held to 64 registers so that
+// four CTAs (32 warps) share an SM and keep their loads in flight; wider tiles are limited by their tensor
+// memory to two CTAs per SM anyway.
 template <int NCOL, int EPI>
-__global__ void __launch_bounds__(kMmaThreads) sno_mma_kernel(const MmaArgs g) {
+__global__ void __launch_bounds__(kMmaThreads, NCOL <= 64 ? 4 : 1) sno_mma_kernel(const MmaArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sA =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
