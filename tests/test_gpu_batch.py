@@ -128,3 +128,49 @@ def test_periodic_batch_matches_oracle(dtype):
         l2 = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         linf = np.abs(got - ref).max() / np.abs(ref).max()
         assert l2 <= tol and linf <= tol, (N, l2, linf)
+
+
+def test_full_size_batch_sampled_problems_match_oracle():
+    """The 512-problem workload (N_x, N_y from 64 to 384, D log-uniform in [1e-4, 1e-2], 200 ETDRK2 steps, FP32)
+    in the launch configuration the bench times (tile sizes and schedule tuned at creation, graph replay), with
+    one sampled problem per x length checked against the FP64 oracle over the whole run (T = 2).
+
+    Bound 1e-4 (the batched workload's stated target is a final-time rel L2 <= 1e-3). Over T = 2 the FP32 floor
+    exceeds the 1e-5 of shorter runs: Allen-Cahn amplifies rounding at rate f'(0) = 1 where diffusion is weak,
+    and even the odd-extension transforms (rounding ~ log N) measure up to 1.8e-5 on these problems; the
+    default FP32 route below N = 512 is the half-length recurrence (rounding ~ sqrt(N/2) eps), measured up to
+    4.6e-5. One plan per problem on the same route gives the same errors (the batch adds nothing); both are
+    reported next to the odd-extension plan's."""
+    from paper_2209_11922_gb300.etd import Batch, Plan
+    bw = inputs.BATCH_2D_512
+    probs = bw.problems()
+    shapes = [(ny - 1, nx - 1) for (nx, ny), _ in probs]
+    U0 = [bw.u0(i, s).astype(np.float32) for i, s in enumerate(shapes)]
+    fields = [torch.from_numpy(u).cuda() for u in U0]
+    with Batch([p[0] for p in probs], [p[1] for p in probs], bw.tau, 2, "f32") as b:
+        b.run(fields, bw.nsteps)
+        torch.cuda.synchronize()
+    sample, seen = [], set()
+    for i, ((nx, ny), _) in enumerate(probs):
+        if nx not in seen:
+            seen.add(nx)
+            sample.append(i)
+    assert len(sample) == 6
+    rows = []
+    for i in sample:
+        (N, D) = probs[i]
+        ref = oetd.run(U0[i].astype(np.float64), N, (1 / N[0], 1 / N[1]), D, bw.tau, bw.nsteps, 2)
+        errs = {}
+        for name, route in (("batch", None), ("plan", "auto"), ("plan_odd", "fft")):
+            if route is None:
+                got = fields[i].cpu().numpy().astype(np.float64)
+            else:
+                with Plan(N, D, bw.tau, 2, "f32", route=route) as pl:
+                    u = torch.from_numpy(U0[i]).cuda()
+                    pl.run(u, bw.nsteps)
+                    got = u.cpu().numpy().astype(np.float64)
+            errs[name] = (np.linalg.norm(got - ref) / np.linalg.norm(ref), np.abs(got - ref).max() / np.abs(ref).max())
+        rows.append((i, N, D, errs))
+        print(f"problem {i} N={N} D={D:.2e}: " + ", ".join(f"{k} rel L2 {v[0]:.2e} Linf {v[1]:.2e}" for k, v in errs.items()))
+    for i, N, D, errs in rows:
+        assert max(errs["batch"]) <= 1e-4, (i, N, D, errs)
