@@ -316,6 +316,7 @@ def run_gb300(args, w):
             # the other configurations of the workload set, measured after the headline (outside its
             # timed region): 256^3 on every route, the split-radix route, the batch and the surrogate
             line["route_fft_split_2d_1024"] = measure_split_route(args)
+            line["config2_arms"] = measure_config2_arms(args)
             line["config3_3d_256cubed"] = measure_3d(args)
             line["config4_batched"] = measure_batched(args, inputs.BATCH_2D_512, 3, 3)
             sno = measure_sno(args, inputs.SNO_256)
@@ -591,8 +592,11 @@ def measure_3d(args) -> dict:
     u0 = torch.from_numpy(w.u0().astype(np.float32)).cuda()
     U0s = ws.u0().astype(np.float32).astype(np.float64)
     ref = oetd.run(U0s, ws.N, ws.h, ws.D, ws.tau, 5, 2)
+    ref_full = oetd.run(U0s, ws.N, ws.h, ws.D, ws.tau, ws.nsteps, 2)
     out = {"workload": w.name, "unknowns": w.unknowns, "time_steps_timed": nsteps,
-           "error_case": f"{ws.name}, 5 steps, rel L2 / rel Linf against the FP64 oracle", "routes": {}}
+           "error_case": f"{ws.name}, 5 steps, rel L2 / rel Linf against the FP64 oracle",
+           "error_case_full": f"{ws.name}, the workload's {ws.nsteps} steps, rel L2 against the FP64 oracle",
+           "routes": {}}
     stream = torch.cuda.current_stream()
     for route, passes in (("auto", 19), ("gemm_tf32", 27), ("gemm_bf16x3", 27)):
         with Plan(w.N, w.D, w.tau, 2, "f32", route=route) as pl:
@@ -616,12 +620,65 @@ def measure_3d(args) -> dict:
             d = torch.from_numpy(U0s.astype(np.float32)).cuda()
             pl.run(d, 5)
             got = d.cpu().numpy().astype(np.float64)
+            d.copy_(torch.from_numpy(U0s.astype(np.float32)))
+            pl.run(d, ws.nsteps)
+            got_full = d.cpu().numpy().astype(np.float64)
         achieved = passes * 4 * w.unknowns / (ms * 1e-3) / 1e9
         out["routes"][route] = {
             "ms_per_time_step": ms, "value": w.unknowns / (ms * 1e-3), "unit": UNIT,
             "field_passes_per_step": passes, "achieved_GBps": achieved, "peak": peak, "peak_source": peak_src,
             "frac": achieved / peak,
             "pass_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in prof.items() if v[1] > 0},
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "rel_linf": float(np.abs(got - ref).max() / np.abs(ref).max()),
+            "rel_l2_full": float(np.linalg.norm(got_full - ref_full) / np.linalg.norm(ref_full))}
+    return out
+
+
+_ORACLE_1024 = {}
+
+
+def _oracle_1024(scheme: int) -> np.ndarray:
+    """The FP64 oracle's first 100 steps of the 1023^2 workload from its FP32-rounded initial field."""
+    from oracle import etd as oetd
+
+    if scheme not in _ORACLE_1024:
+        w = inputs.AC2D_1024
+        U0 = w.u0().astype(np.float32).astype(np.float64)
+        _ORACLE_1024[scheme] = oetd.run(U0, w.N, w.h, w.D, w.tau, 100, scheme)
+    return _ORACLE_1024[scheme]
+
+
+def measure_config2_arms(args) -> dict:
+    """The 1023^2 workload's other arms (ETDRK1; FP64 transforms), beside the FP32 ETDRK2 headline: time per
+    time step over a 200-step run after warm-up, and the error of the first 100 steps against the FP64
+    oracle (rel L2 / rel Linf)."""
+    import torch
+
+    from paper_2209_11922_gb300.etd import Plan
+
+    w = inputs.AC2D_1024
+    stream = torch.cuda.current_stream()
+    out = {"workload": w.name, "time_steps_timed": 200,
+           "error_case": "first 100 steps, rel L2 / rel Linf against the FP64 oracle"}
+    for dtype, scheme in (("f32", 1), ("f64", 2), ("f64", 1)):
+        ref = _oracle_1024(scheme)
+        U0 = w.u0().astype(np.float32).astype(np.float64 if dtype == "f64" else np.float32)
+        with Plan(w.N, w.D, w.tau, scheme, dtype) as pl:
+            u = torch.from_numpy(U0).cuda()
+            pl.run(u, 100)
+            got = u.cpu().numpy().astype(np.float64)
+            u.copy_(torch.from_numpy(U0))
+            pl.run(u, 40, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pl.run(u, 200, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 200
+        out[f"{dtype}_etdrk{scheme}"] = {
+            "ms_per_time_step": ms, "value": w.unknowns / (ms * 1e-3), "unit": UNIT,
             "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
             "rel_linf": float(np.abs(got - ref).max() / np.abs(ref).max())}
     return out
@@ -632,12 +689,11 @@ def measure_split_route(args) -> dict:
     step over a 2000-step run and the error of 100 steps against the FP64 oracle, both routes."""
     import torch
 
-    from oracle import etd as oetd
     from paper_2209_11922_gb300.etd import Plan
 
     w = inputs.AC2D_1024
     U0 = w.u0().astype(np.float32)
-    ref = oetd.run(U0.astype(np.float64), w.N, w.h, w.D, w.tau, 100, 2)
+    ref = _oracle_1024(2)
     stream = torch.cuda.current_stream()
     out = {"workload": w.name, "error_case": "100 ETDRK2 steps, rel L2 / rel Linf against the FP64 oracle"}
     for route in ("auto", "fft_split"):
