@@ -221,9 +221,10 @@ def test_full_size_2d_1024_first_steps(dtype, scheme):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_full_size_2d_1024_first_100_steps(dtype):
-    """The first 100 ETDRK2 steps of the 1024^2 workload (T = 0.5) stay within the tolerance."""
-    _full_size(inputs.AC2D_1024, dtype, 100, 2)
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_full_size_2d_1024_first_100_steps(dtype, scheme):
+    """The first 100 steps of the 1024^2 workload (T = 0.5), ETDRK1 and ETDRK2, stay within the tolerance."""
+    _full_size(inputs.AC2D_1024, dtype, 100, scheme)
 
 
 def test_full_size_3d_256_first_step():
