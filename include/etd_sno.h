@@ -61,10 +61,11 @@ etd_status etd_sno_destroy(etd_sno s);
 
 /* Parareal over `windows` windows of `window_steps` ETDRK2 steps of size tau, for B problems at N x N
  * with coefficients D[B] (host): U_0 = u0, U_{n+1}^{k+1} = G(U_n^{k+1}) + F(U_n^k) - G(U_n^k) from the
- * coarse sweep U^0. F runs every window of every problem as one batched ETDRK2 launch sequence
- * (windows x B problems); G is the SNO (sno != NULL, trained for window_steps steps) or, for
+ * coarse sweep U^0. F runs the windows not yet converged of every problem as one batched ETDRK2 launch
+ * sequence; G is the SNO (sno != NULL, trained for window_steps steps) or, for
  * sno == NULL, one ETDRK2 step of size window_steps * tau. Creation builds (and autotunes) the
- * batched solvers; it allocates states for all windows. */
+ * batched solvers, one fine solver per count of windows still to converge (an iteration propagates only
+ * those); it allocates states for all windows. */
 typedef struct etd_parareal_s* etd_parareal;
 etd_status etd_parareal_create(etd_parareal* out, etd_sno sno, int N, int B, const double* D, double tau,
                                int window_steps, int windows);

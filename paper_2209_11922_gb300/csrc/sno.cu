@@ -577,7 +577,9 @@ struct etd_parareal_s {
   long long npix = 0;
   double tau = 0;
   std::vector<double> D;
-  etd_batch fine_all = nullptr;   // W * B problems (window n of problem b at n * B + b)
+  // fine[k]: the windows k .. W-1 of every problem, (W - k) * B problems (window n of problem b at
+  // (n - k) * B + b); an iteration propagates only the windows not yet converged
+  std::vector<etd_batch> fine;
   etd_batch fine_one = nullptr;   // B problems (fallback)
   etd_batch coarse = nullptr;     // B problems, one step of steps * tau (no SNO)
   float* U = nullptr;             // (W + 1) * B fields: current iterate
@@ -642,7 +644,9 @@ etd_status etd_parareal_create(etd_parareal* out, etd_sno sno, int N, int B, con
     return st;
   };
   etd_status st;
-  if ((st = make_batch(&p->fine_all, windows * B, N, D, B, tau)) != ETD_OK) return bail(st);
+  p->fine.assign(windows, nullptr);
+  for (int k = 0; k < windows; ++k)
+    if ((st = make_batch(&p->fine[k], (windows - k) * B, N, D, B, tau)) != ETD_OK) return bail(st);
   if ((st = make_batch(&p->fine_one, B, N, D, B, tau)) != ETD_OK) return bail(st);
   if (!sno && (st = make_batch(&p->coarse, B, N, D, B, tau * window_steps)) != ETD_OK) return bail(st);
   const size_t fb = (size_t)B * p->npix * sizeof(float);
@@ -680,10 +684,12 @@ etd_status etd_parareal_run(etd_parareal p, const float* u0, float* u_out, int m
   // propagator's rounding (bf16 in the operator, not Lipschitz in its input) to converged states.
   int d = 0;
   for (int k = 1; k <= max_iter && d < W; ++k) {
-    // fine propagation of every window of the current iterate, in one batched run
-    SNO_CUDA(cudaMemcpyAsync(p->F, p->U, W * fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    for (int i = 0; i < W * B; ++i) p->ptr_all[i] = p->F + (size_t)i * p->npix;
-    SNO_TRY(etd_batch_run(p->fine_all, p->ptr_all.data(), p->steps, s));
+    // fine propagation of the windows d .. W-1 of the current iterate (the earlier ones are converged), in
+    // one batched run
+    SNO_CUDA(cudaMemcpyAsync(win(p->F, d), win(p->U, d), (size_t)(W - d) * fe * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < (W - d) * B; ++i) p->ptr_all[i] = win(p->F, d) + (size_t)i * p->npix;
+    SNO_TRY(etd_batch_run(p->fine[d], p->ptr_all.data(), p->steps, s));
     // sequential correction sweep
     SNO_CUDA(cudaMemcpyAsync(p->V, p->U, (size_t)(d + 1) * fe * sizeof(float), cudaMemcpyDeviceToDevice, s));
     double worst = 0.0;
@@ -732,7 +738,8 @@ etd_status etd_parareal_run(etd_parareal p, const float* u0, float* u_out, int m
 
 etd_status etd_parareal_destroy(etd_parareal p) {
   if (!p) return ETD_OK;
-  if (p->fine_all) etd_batch_destroy(p->fine_all);
+  for (etd_batch f : p->fine)
+    if (f) etd_batch_destroy(f);
   if (p->fine_one) etd_batch_destroy(p->fine_one);
   if (p->coarse) etd_batch_destroy(p->coarse);
   for (void* q : {(void*)p->U, (void*)p->V, (void*)p->F, (void*)p->Go, (void*)p->Gn, (void*)p->part})
