@@ -141,7 +141,10 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
 /* Advance the device field u (in place) by `nsteps` >= 0 time steps on `stream`. nsteps = 0 is a
  * no-op. Equivalent to nsteps calls of etd_step up to rounding (the internal state between steps
  * stays spectral along all axes but the last, or all axes on the GEMM routes). Errors: ETD_ERR_INVALID_ARG (plan or u NULL,
- * nsteps < 0), ETD_ERR_CUDA. */
+ * nsteps < 0), ETD_ERR_CUDA.
+ * Runs (plans and batches) replay steady-state steps from a CUDA graph of ETD_GRAPH_STEPS time steps
+ * (environment variable, default 32; 0: every step as direct launches), and pass kernels launch with
+ * programmatic dependent launch unless ETD_PDL=0. Both change only timing, not results. */
 etd_status etd_run(etd_plan plan, void* u, int64_t nsteps, void* stream);
 
 /* One time step: etd_run(plan, u, 1, stream). */

@@ -674,13 +674,10 @@ etd_status make_gemm_launch(etd_plan_s* pl, int a, const void* in, const void* i
   const int R = (int)(pl->nfield / (size_t)K);
   const int route = pl->gemm - 1;
   const int mt = (R + 127) / 128;
-  int bn = env_int("ETD_GEMM_BN", 0);
-  if (bn != 32 && bn != 64 && bn != 128 && bn != 256) {
-    // widest tile that still gives every SM a CTA (wider tiles re-read the field fewer times)
-    bn = 256;
-    while (bn > K) bn /= 2;
-    while (bn > 64 && (long long)mt * ((K + bn - 1) / bn) < pl->num_sms) bn /= 2;
-  }
+  // widest tile that still gives every SM a CTA (wider tiles re-read the field fewer times)
+  int bn = 256;
+  while (bn > K) bn /= 2;
+  while (bn > 64 && (long long)mt * ((K + bn - 1) / bn) < pl->num_sms) bn /= 2;
   if (bn > K) bn = 32;
   const GemmKernelInfo* k = find_gemm_kernel(bn, route);
   if (!k) return fail(ETD_ERR_UNSUPPORTED, "no tensor-core pass for tile width %d", bn);
