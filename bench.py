@@ -264,7 +264,12 @@ def run_gb300(args, w):
     step_kinds = {k: v for k, v in kinds.items() if k not in ("entry_exit", "pack", "monitor")}
     dom = max(step_kinds, key=lambda k: step_kinds[k][0])
     dom_ms, dom_n = step_kinds[dom]
-    rw = {"x_react": 2, "transform": 2, "stage1_etdrk2": 4, "stage2_etdrk2": 3, "stage_etdrk1": 3}[dom]
+    # the FFT routes keep the state also transformed along the last axis: their closing stage pass writes
+    # it as a second output (the split-radix route, whose last axis has no such pass, and the GEMM
+    # routes do not)
+    spec = args.route in ("auto", "fft", "fft_half")
+    rw = {"x_react": 2, "transform": 2, "stage1_etdrk2": 4, "stage2_etdrk2": 4 if spec else 3,
+          "stage_etdrk1": 4 if spec else 3}[dom]
     esz = 4 if dtype == "f32" else 8
     alg_bytes = rw * w.unknowns * esz
     achieved = alg_bytes / (dom_ms * 1e-3 / dom_n) / 1e9
@@ -287,7 +292,8 @@ def run_gb300(args, w):
 
     if rank == 0:
         clocks = clk.summary()
-        entry_exit = 2 if len(w.N) == 2 else 4   # entry + exit launches per run
+        # entry + exit launches per run (2D: entry, last-axis transform of the state, exit; 3D: two more)
+        entry_exit = (2 if len(w.N) == 2 else 4) + (1 if spec else 0)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -421,14 +427,16 @@ def measure_batched(args, bw, steps: int, warmup: int, nsteps: int = 0) -> dict:
                         row[route]["rel_l2_vs_fft_20_steps"] = float((v.double() - ref_u).norm() / ref_u.norm())
             per_len[str(n)] = row
     esz = 4 if dtype == "f32" else 8
-    achieved = 11 * unknowns * esz / (ms / steps / nsteps * 1e-3) / 1e9
+    achieved = 12 * unknowns * esz / (ms / steps / nsteps * 1e-3) / 1e9   # field passes per time step
     peak, peak_src = _peaks()
     return {"workload": bw.name, "problems": len(probs), "unknowns": unknowns, "time_steps_per_run": nsteps,
             "value": value, "unit": UNIT, "ms_per_run": ms / steps, "plans_value": value_plans,
             "speedup_vs_plans": value / value_plans, "launches_per_time_step": info["launches_per_step"],
             "tuned_tile_pairs": info["tile_pairs"], "schedule": sched, "create_s": round(create_s, 3),
             "route_per_length": per_len, "runs_timed": steps,
-            "gpu_launches": steps * (info["launches_per_step"] * nsteps + 12),
+            # per run: entry (one group per x length), the state's y transform (one per y length), exit (per
+            # x length), six lengths each
+            "gpu_launches": steps * (info["launches_per_step"] * nsteps + 18),
             "roofline": {"bound": "hbm", "kernel": "one time step (all grouped launches)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": None}}
@@ -579,7 +587,7 @@ def measure_3d(args) -> dict:
     """The 256^3 Allen-Cahn workload (255^3 unknowns, D = 1e-3, tau = 1e-2, ETDRK2, FP32) on each
     transform route: time per ETDRK2 step (events around a run of time steps after warm-up runs; the
     330 MB of fields exceed L2), unknown-updates/s, the step-level fraction of HBM bandwidth on the
-    pass schedule's field passes (FFT routes 19 per step, GEMM routes 27, 4 bytes each), and the route's
+    pass schedule's field passes (FFT routes 20 per step, GEMM routes 27, 4 bytes each), and the route's
     error against the oracle on the same configuration at 64^3 (63^3 unknowns, 5 steps)."""
     import torch
 
@@ -598,7 +606,7 @@ def measure_3d(args) -> dict:
            "error_case_full": f"{ws.name}, the workload's {ws.nsteps} steps, rel L2 against the FP64 oracle",
            "routes": {}}
     stream = torch.cuda.current_stream()
-    for route, passes in (("auto", 19), ("gemm_tf32", 27), ("gemm_bf16x3", 27)):
+    for route, passes in (("auto", 20), ("gemm_tf32", 27), ("gemm_bf16x3", 27)):
         with Plan(w.N, w.D, w.tau, 2, "f32", route=route) as pl:
             u = torch.empty_like(u0)
             for _ in range(2):

@@ -123,7 +123,8 @@ etd_status etd_options_default(etd_options* opt);
 /*
  * Create a plan for `ndim` in {2, 3} axes with N[a] intervals (N[0] = N_x, the fastest axis) of
  * size h[a] > 0, diffusion D > 0 and time step tau > 0 (Section 2.2, uniform tau_n = tau).
- * Allocates the device workspace (five fields of N_x*N_y[*N_z] elements) and the FP64-derived
+ * Allocates the device workspace (six fields of N_x*N_y[*N_z] elements on the FFT routes, five on the
+ * GEMM routes and where the last axis runs the split-radix kernels) and the FP64-derived
  * tables (eigenvalues mu_a, exp(-tau D mu_a), exp(-c2 tau D mu_a), twiddles) on the current
  * device, and uploads them. Supported N[a]: 2^k (4..2048) and 3*2^k (6..1536).
  * Periodic plans (opt->bc = ETD_BC_PERIODIC) run the Hartley kernels on every FFT route (AUTO,

@@ -123,7 +123,8 @@ struct etd_plan_s {
   int device = 0;
   int num_sms = 148;
   void* ws = nullptr;      // fields
-  void* F[5] = {};         // V, N0, V2, P, N2
+  void* F[6] = {};         // V, N0, V2, P, N2, and (spec) V~: V transformed along the last axis
+  bool spec = false;       // the step keeps V~ and runs the stage passes on it (RK1S, S1S, S2S)
   void* tables = nullptr;
   const void* tw[3] = {};
   const void* stw[3] = {};   // twiddle tables of the split-radix kernels (split axes)
@@ -266,12 +267,12 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   a.sc = (T)pl->sc[axis];
   if constexpr (sizeof(T) == 4) {
     if (pl->coef && pl->ndim == 2 && axis == 1) {
-      if (op == OP_S1) a.coef = pl->coef + pl->coef_s1;
-      else if (op == OP_S2) a.coef = pl->coef + pl->coef_s2;
-      else if (op == OP_RK1) a.coef = pl->coef + pl->coef_rk1;
+      if (op == OP_S1 || op == OP_S1S) a.coef = pl->coef + pl->coef_s1;
+      else if (op == OP_S2 || op == OP_S2S) a.coef = pl->coef + pl->coef_s2;
+      else if (op == OP_RK1 || op == OP_RK1S) a.coef = pl->coef + pl->coef_rk1;
     }
   }
-  const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
+  const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2 || op == OP_RK1S || op == OP_S1S || op == OP_S2S);
   const int maxp = 512 / k->tpp > 0 ? 512 / k->tpp : 1;
   int P = 1;
   long long grid = 0;
@@ -316,7 +317,7 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   }
   a.P = P;
   a.lp = pair_stride(*k, P);
-  L.fn = (op >= 0 && op < 9 && k->fn_op[op]) ? k->fn_op[op] : k->fn;
+  L.fn = (op >= 0 && op < OP_COUNT && k->fn_op[op]) ? k->fn_op[op] : k->fn;
   L.grid = dim3((unsigned)grid);
   L.block = dim3((unsigned)(P * k->tpp));
   L.smem = pass_smem_bytes(*k, P, two ? 2 : 1);
@@ -332,7 +333,7 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   // the weights per mode. Longer axes read the tables from global memory.
   if constexpr (sizeof(T) == 4) {
     if (a.coef && two && k->min_blocks == 1 && k->N <= 1536) {
-      const int fpm = op == OP_S1 ? 2 : 1;
+      const int fpm = (op == OP_S1 || op == OP_S1S) ? 2 : 1;
       const size_t need = L.smem - (size_t)N * sizeof(float) + 16 + (size_t)N * 2 * P * fpm * sizeof(float);
       if ((2 * P * fpm) % 4 == 0 && need <= (size_t)optin) {
         a.coef_smem = 1;
@@ -468,10 +469,18 @@ etd_status append_boundary(etd_plan_s* pl, int stage, void* target, std::vector<
 template <class T>
 etd_status build_step(etd_plan_s* pl) {
   void** F = pl->F;
-  enum { V = 0, N0 = 1, V2 = 2, PF = 3, N2 = 4 };
+  enum { V = 0, N0 = 1, V2 = 2, PF = 3, N2 = 4, VS = 5 };
   pl->step.clear();
   Launch L;
   etd_status st;
+  // The stage passes of the last axis: on plans that keep V~ (V transformed along the last axis, written
+  // by the step's last pass) they read it instead of transforming V, one DST fewer per step for one more
+  // field written.
+  const bool sp = pl->spec;
+  const int op_s1 = sp ? OP_S1S : OP_S1, op_s2 = sp ? OP_S2S : OP_S2, op_rk1 = sp ? OP_RK1S : OP_RK1;
+  void* const s1_in = sp ? F[VS] : F[V];
+  void* const s2_out1 = sp ? F[VS] : nullptr;
+  const double s2_rw = sp ? 4 : 3;
 #define ADD(op, axis, i0, i1, o0, o1, kind, rw)                                               \
   do {                                                                                         \
     st = make_launch<T>(pl, op, axis, i0, i1, o0, o1, kind, rw, L);                            \
@@ -487,14 +496,14 @@ etd_status build_step(etd_plan_s* pl) {
     if (pl->scheme == 2) {
       ADD(OP_REACT, 0, F[V], nullptr, F[N0], nullptr, PK_REACT, 2);
       BND(0, F[N0]);
-      ADD(OP_S1, 1, F[V], F[N0], F[V2], F[PF], PK_S1, 4);
+      ADD(op_s1, 1, s1_in, F[N0], F[V2], F[PF], PK_S1, 4);
       ADD(OP_REACT, 0, F[V2], nullptr, F[N2], nullptr, PK_REACT, 2);
       BND(1, F[N2]);
-      ADD(OP_S2, 1, F[N2], F[PF], F[V], nullptr, PK_S2, 3);
+      ADD(op_s2, 1, F[N2], F[PF], F[V], s2_out1, PK_S2, s2_rw);
     } else {
       ADD(OP_REACT, 0, F[V], nullptr, F[N0], nullptr, PK_REACT, 2);
       BND(0, F[N0]);
-      ADD(OP_RK1, 1, F[V], F[N0], F[V], nullptr, PK_RK1, 3);
+      ADD(op_rk1, 1, s1_in, F[N0], F[V], s2_out1, PK_RK1, s2_rw);
     }
   } else {
     ADD(OP_TRANSFORM, 1, F[V], nullptr, F[V2], nullptr, PK_TRANSFORM, 2);
@@ -502,14 +511,14 @@ etd_status build_step(etd_plan_s* pl) {
     ADD(OP_TRANSFORM, 1, F[N0], nullptr, F[N0], nullptr, PK_TRANSFORM, 2);
     BND(0, F[N0]);
     if (pl->scheme == 2) {
-      ADD(OP_S1, 2, F[V], F[N0], F[V2], F[PF], PK_S1, 4);
+      ADD(op_s1, 2, s1_in, F[N0], F[V2], F[PF], PK_S1, 4);
       ADD(OP_TRANSFORM, 1, F[V2], nullptr, F[V2], nullptr, PK_TRANSFORM, 2);
       ADD(OP_REACT, 0, F[V2], nullptr, F[N2], nullptr, PK_REACT, 2);
       ADD(OP_TRANSFORM, 1, F[N2], nullptr, F[N2], nullptr, PK_TRANSFORM, 2);
       BND(1, F[N2]);
-      ADD(OP_S2, 2, F[N2], F[PF], F[V], nullptr, PK_S2, 3);
+      ADD(op_s2, 2, F[N2], F[PF], F[V], s2_out1, PK_S2, s2_rw);
     } else {
-      ADD(OP_RK1, 2, F[V], F[N0], F[V], nullptr, PK_RK1, 3);
+      ADD(op_rk1, 2, s1_in, F[N0], F[V], s2_out1, PK_RK1, s2_rw);
     }
   }
 #undef BND
@@ -530,6 +539,11 @@ etd_status entry_exit(etd_plan_s* pl, bool entry, void* u, std::vector<Launch>& 
     out.push_back(L);
     if (pl->ndim == 3) {
       st = make_launch<T>(pl, OP_TRANSFORM, 1, F[0], nullptr, F[0], nullptr, PK_ENTRY_EXIT, 2, L);
+      if (st != ETD_OK) return st;
+      out.push_back(L);
+    }
+    if (pl->spec) {   // V~ for the first step's stage pass
+      st = make_launch<T>(pl, OP_TRANSFORM, pl->ndim - 1, F[0], nullptr, F[5], nullptr, PK_ENTRY_EXIT, 2, L);
       if (st != ETD_OK) return st;
       out.push_back(L);
     }
@@ -1225,7 +1239,7 @@ etd_status batch_build_op(etd_batch_s* b, const std::vector<BatchTables>& tabs, 
     const int odd = o.axis == 0 ? b->oddx[g.inst[0]] : b->oddy[g.inst[0]];
     const KernelInfo* k = find_pass_kernel((int)sizeof(T), g.N, odd);
     if (!k) return fail(ETD_ERR_UNSUPPORTED, "no kernel for axis length %d", g.N);
-    g.fn = (o.op >= 0 && o.op < 9 && k->fn_batched_op[o.op]) ? k->fn_batched_op[o.op] : k->fn_batched;
+    g.fn = (o.op >= 0 && o.op < OP_COUNT && k->fn_batched_op[o.op]) ? k->fn_batched_op[o.op] : k->fn_batched;
     g.tpp = k->tpp;
     long long unk = 0;
     const int cut = b->periodic ? 0 : 1;
@@ -1422,7 +1436,7 @@ etd_status batch_build(etd_batch_s* b) {
   b->field_off.resize(b->count);
   for (int i = 0; i < b->count; ++i) {
     b->field_off[i] = total;
-    total += 5 * (size_t)b->nx[i] * b->ny[i];
+    total += 6 * (size_t)b->nx[i] * b->ny[i];   // V, N0, V2, P, N2, V~
     total = (total + 63) & ~(size_t)63;   // 256-byte aligned fields
     const int cut = b->periodic ? 0 : 1;
     b->unknowns += (int64_t)(b->nx[i] - cut) * (b->ny[i] - cut);
@@ -1440,15 +1454,17 @@ etd_status batch_build(etd_batch_s* b) {
   b->aux_bytes = (size_t)nops * ((size_t)b->count * sizeof(PassArgs<T>) + tiles1 * sizeof(int2)) + (size_t)nops * 64 * 512;
   ETD_CUDA(cudaMalloc(&b->d_aux, b->aux_bytes));
   char* aux = static_cast<char*>(b->d_aux);
-  enum { V = 0, N0 = 1, V2 = 2, PF = 3, N2 = 4 };
+  // the step of a single plan with the spectral state V~ (y-transformed V): the stage passes read V~
+  // instead of transforming V, the last pass writes both
+  enum { V = 0, N0 = 1, V2 = 2, PF = 3, N2 = 4, VS = 5 };
   std::vector<BatchOp> ops;
   if (b->scheme == 2) {
     ops = {{OP_REACT, 0, V, -1, N0, -1, PK_REACT, 1, 2.0},
-           {OP_S1, 1, V, N0, V2, PF, PK_S1, 2, 4.0},
+           {OP_S1S, 1, VS, N0, V2, PF, PK_S1, 2, 4.0},
            {OP_REACT, 0, V2, -1, N2, -1, PK_REACT, 1, 2.0},
-           {OP_S2, 1, N2, PF, V, -1, PK_S2, 2, 3.0}};
+           {OP_S2S, 1, N2, PF, V, VS, PK_S2, 2, 4.0}};
   } else {
-    ops = {{OP_REACT, 0, V, -1, N0, -1, PK_REACT, 1, 2.0}, {OP_RK1, 1, V, N0, V, -1, PK_RK1, 2, 3.0}};
+    ops = {{OP_REACT, 0, V, -1, N0, -1, PK_REACT, 1, 2.0}, {OP_RK1S, 1, VS, N0, V, VS, PK_RK1, 2, 4.0}};
   }
   const bool autotune = env_int("ETD_AUTOTUNE", 1) != 0;
   std::map<long long, int> tuned;
@@ -1459,7 +1475,10 @@ etd_status batch_build(etd_batch_s* b) {
     for (size_t q = first; q < b->step.size(); ++q) b->step[q].pass = (int)oi;
   }
   const BatchOp ent{OP_ENTRY, 0, -1, -1, V, -1, PK_ENTRY_EXIT, 1, 2.0}, ext{OP_EXIT, 0, V, -1, -1, -1, PK_ENTRY_EXIT, 1, 2.0};
+  const BatchOp ent_s{OP_TRANSFORM, 1, V, -1, VS, -1, PK_ENTRY_EXIT, 1, 2.0};
   etd_status st = batch_build_op<T>(b, tabs, ent, b->entry, aux, tuned, false);
+  if (st != ETD_OK) return st;
+  st = batch_build_op<T>(b, tabs, ent_s, b->entry, aux, tuned, false);
   if (st != ETD_OK) return st;
   st = batch_build_op<T>(b, tabs, ext, b->exit_, aux, tuned, false);
   if (st != ETD_OK) return st;
@@ -1640,12 +1659,16 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   if (cudaGetDevice(&pl->device) != cudaSuccess) return bail(fail(ETD_ERR_CUDA, "no CUDA device"));
   cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
   const size_t fbytes = pl->nfield * pl->elem;
-  pl->ws_bytes = 5 * fbytes;
+  // FFT routes keep V~ (a sixth field), except where the last axis runs the split-radix kernels,
+  // which have no stage passes on it
+  pl->spec = !gemm && !pl->split[ndim - 1];
+  const int nf = pl->spec ? 6 : 5;
+  pl->ws_bytes = nf * fbytes;
   cudaError_t e = cudaMalloc(&pl->ws, pl->ws_bytes);
   if (e != cudaSuccess) return bail(fail(ETD_ERR_OOM, "workspace of %zu bytes: %s", pl->ws_bytes, cudaGetErrorString(e)));
   e = cudaMemset(pl->ws, 0, pl->ws_bytes);
   if (e != cudaSuccess) return bail(fail(ETD_ERR_CUDA, "memset: %s", cudaGetErrorString(e)));
-  for (int f = 0; f < 5; ++f) pl->F[f] = static_cast<char*>(pl->ws) + f * fbytes;
+  for (int f = 0; f < nf; ++f) pl->F[f] = static_cast<char*>(pl->ws) + f * fbytes;
   etd_status st = (pl->elem == 4) ? upload_tables<float>(pl) : upload_tables<double>(pl);
   if (st != ETD_OK) return bail(st);
   // per-mode phi-function weights of the y passes of 2D FP32 plans on the FFT routes (at most 64 MiB)

@@ -21,6 +21,11 @@
 //             P = e^{-z} U~ + tau (phi1 - phi2/c2)(-z) N0~ (-> out1)               -> eq. (2.14)
 //   S2        last axis: DST(N2), U~+ = P + tau/c2 phi2(-z) N2~, DST               -> eq. (2.14)
 // with z = tau D (mu_x + mu_y [+ mu_z]) per mode (the tensor H of Section 4 times tau).
+// Plans that keep the state also in its fully spectral form U~ (the last-axis DST of U, written by
+// the step's last pass) run the stage passes without the forward DST of U:
+//   RK1S      last axis: in U~, N0; DST(N0), U~+ (-> out1), DST -> U+ (out0)
+//   S1S       last axis: in U~, N0; DST(N0), U2~ and P as S1 (P -> out1), DST -> U2 (out0)
+//   S2S       last axis: as S2, and U~+ (-> out1) before the closing DST
 #pragma once
 #include <type_traits>
 
@@ -39,6 +44,10 @@ enum PassOp : int {
   OP_S2 = 6,
   OP_PACK = 7,
   OP_UNPACK = 8,
+  OP_RK1S = 9,
+  OP_S1S = 10,
+  OP_S2S = 11,
+  OP_COUNT = 12,
 };
 
 enum EpiKind : int { EPI_PLAIN = 0, EPI_REACT = 1, EPI_RK1 = 2, EPI_S1 = 3, EPI_S2 = 4 };
@@ -143,7 +152,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   const T* __restrict__ sn = A.sn;
   C* b0 = tws + ((TWN + 1) & ~1);
   const int op = OPC >= 0 ? OPC : A.op;
-  const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2);
+  const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2 || op == OP_RK1S || op == OP_S1S || op == OP_S2S);
   C* b1 = b0 + A.P * LP;
   C* scr = b0 + (two ? 2 : 1) * A.P * LP;
   // spectral passes (two buffers) also stage the transformed axis's e, ec, zeta tables (3 N values);
@@ -329,7 +338,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   if (coef_smem) {
     // rows j < N of the tile's 2P x modes, fpm floats per mode, as 16-byte chunks stored chunk-major
     // ([chunk c][row j]: the lanes of a warp, consecutive j, then read consecutive chunks)
-    const int fpm = op == OP_S1 ? 2 : 1;
+    const int fpm = (op == OP_S1 || op == OP_S1S) ? 2 : 1;
     const int cpr = 2 * A.P * fpm / 4;
     for (int i = tid; i < N * cpr; i += NT) {
       const int j = i / cpr, c = i - j * cpr;
@@ -362,7 +371,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   const T* zj = tz;   // staged copies of A.zeta[la], A.ex[la], A.ec[la]
   const T* ej = te;
   const T* cj = tcs;
-  if (op == OP_RK1 || op == OP_S1 || op == OP_S2) {
+  if (two) {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int x = x0 + 2 * p + s;
@@ -377,16 +386,21 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     }
   }
 
-  // ---- DST program
-  int nd = 0, bsel[3] = {0, 0, 0}, epi[3] = {EPI_PLAIN, EPI_PLAIN, EPI_PLAIN};
+  // ---- DST program: transforms s0 .. nd-1 of buffer bsel[s], each followed by epilogue epi[s]; the
+  // passes with a spectral input (RK1S, S1S) start after the forward DST of U
+  int nd = 0, s0 = 0, bsel[3] = {0, 0, 0}, epi[3] = {EPI_PLAIN, EPI_PLAIN, EPI_PLAIN};
   switch (op) {
     case OP_ENTRY: case OP_EXIT: case OP_TRANSFORM: nd = 1; break;
     case OP_REACT: nd = 2; break;   // the reaction is applied as the second transform reads
-    case OP_RK1: nd = 3; bsel[1] = 1; epi[1] = EPI_RK1; break;
-    case OP_S1: nd = 3; bsel[1] = 1; epi[1] = EPI_S1; break;
-    case OP_S2: nd = 2; epi[0] = EPI_S2; break;
+    case OP_RK1: case OP_RK1S: nd = 3; bsel[1] = 1; epi[1] = EPI_RK1; break;
+    case OP_S1: case OP_S1S: nd = 3; bsel[1] = 1; epi[1] = EPI_S1; break;
+    case OP_S2: case OP_S2S: nd = 2; epi[0] = EPI_S2; break;
     default: break;
   }
+  if (op == OP_RK1S || op == OP_S1S) s0 = 1;
+  // the spectral result that a pass stores after its stage epilogue (out1): P (S1, S1S, in b1) or U~+
+  // (RK1S, S2S, in b0, before the closing DST)
+  const int spec_out = (op == OP_S1 || op == OP_S1S) ? 1 : ((op == OP_RK1S || op == OP_S2S) ? 0 : -1);
   C* const b0p = b0 + p * LP;
   C* const b1p = b1 + p * LP;
   C* const scrp = scr + p * (TPP > 32 ? TPP / 32 : 1);
@@ -507,7 +521,6 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   // Odd-extension kernels with the full register budget (one CTA of 512 threads per SM) run the
   // two forward transforms of RK1/S1 (of U and of N0) together, sharing each Stockham pass's
   // barriers; under the halved budget the second set of butterfly registers would spill.
-  int s0 = 0;
   if constexpr (L::ODD && pass_min_blocks<T, N, VAR>() == 1) {
     if (op == OP_RK1 || op == OP_S1) {
       C* const bps[2] = {b0p, b1p};
@@ -536,8 +549,11 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     }
     const React<T> rx{op == OP_REACT && s == 1 && !logr, A.flin, A.fcub};
     dst_pair<T, N, VAR>(bp, tw, sn, l, scrp, A.sc, rx);
-    if (kind != EPI_PLAIN) stage_epilogue(kind, bp);
-    if (op == OP_S1 && s == 1) store_tile(b1, A.out1);
+    if (kind != EPI_PLAIN) {
+      stage_epilogue(kind, bp);
+      // (the closing DST of b0 reads the buffer before its first barrier and writes after it)
+      if (spec_out >= 0) store_tile(spec_out ? b1 : b0, A.out1);
+    }
   }
 
   if (op == OP_REACT && A.src_gx) {
@@ -614,8 +630,8 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N, VAR>())
 struct KernelInfo {
   const void* fn;
   const void* fn_batched;
-  const void* fn_op[9];   // kernels with the operation fixed, by PassOp (NULL: use fn)
-  const void* fn_batched_op[9];   // the same for batches (NULL: use fn_batched)
+  const void* fn_op[OP_COUNT];           // kernels with the operation fixed, by PassOp (NULL: use fn)
+  const void* fn_batched_op[OP_COUNT];   // the same for batches (NULL: use fn_batched)
   int N;
   int tpp;
   int lp;
@@ -637,21 +653,22 @@ template <class T, int N, int VAR> KernelInfo kernel_info() {
   using L = PairLayout<T, N, VAR>;
   KernelInfo k{reinterpret_cast<const void*>(&pass_kernel<T, N, VAR>),
                reinterpret_cast<const void*>(&pass_kernel_batched<T, N, VAR>),
-               {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
-               {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+               {},
+               {},
                N, L::TPP, L::LP, (int)sizeof(T), L::M,
                VAR, L::PADG, L::TWN, {0, 0, 0, 0}, pass_min_blocks<T, N, VAR>()};
   if constexpr (pass_op_kernels<T, N, VAR>()) {
+    // single plans run the stage passes on the spectral state (RK1S, S1S, S2S)
     k.fn_op[OP_REACT] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_REACT>);
     k.fn_op[OP_TRANSFORM] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_TRANSFORM>);
-    k.fn_op[OP_RK1] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_RK1>);
-    k.fn_op[OP_S1] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S1>);
-    k.fn_op[OP_S2] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S2>);
-    // batches are 2D: no TRANSFORM passes
+    k.fn_op[OP_RK1S] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_RK1S>);
+    k.fn_op[OP_S1S] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S1S>);
+    k.fn_op[OP_S2S] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S2S>);
+    // batches are 2D: TRANSFORM only at entry (the generic kernel)
     k.fn_batched_op[OP_REACT] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_REACT>);
-    k.fn_batched_op[OP_RK1] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_RK1>);
-    k.fn_batched_op[OP_S1] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S1>);
-    k.fn_batched_op[OP_S2] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S2>);
+    k.fn_batched_op[OP_RK1S] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_RK1S>);
+    k.fn_batched_op[OP_S1S] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S1S>);
+    k.fn_batched_op[OP_S2S] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S2S>);
   }
   radix_list(k.radix, typename L::Plan::R{});
   return k;

@@ -303,12 +303,14 @@ def _ref3d(n):
     return _REF3D[n]
 
 
-@pytest.mark.parametrize("dtype,steps,tol", [("f64", 500, 1e-12), ("f32", 100, 1e-5), ("f32", 500, 1e-4)])
+@pytest.mark.parametrize("dtype,steps,tol", [("f64", 100, 1e-12), ("f64", 500, 2e-12), ("f32", 100, 1e-5),
+                                             ("f32", 500, 1e-4)])
 def test_3d_64_full_horizon(dtype, steps, tol):
     """The 3D workload's error case (63^3 unknowns, D = 1e-3, tau = 1e-2) over the workload's whole horizon, 500
-    ETDRK2 steps (T = 5), against the oracle. FP64 holds 1e-12 throughout; FP32 holds 1e-5 to 100 steps. Over
-    T = 5 the Allen-Cahn growth rate f'(0) = 1 amplifies FP32 rounding: the default route measures 2.9e-5 (rel
-    L2) / 4.8e-5 (rel Linf) and the odd-extension route 2.7e-5 / 4.1e-5 alike, so the FP32 500-step bound is 1e-4."""
+    ETDRK2 steps (T = 5), against the oracle. FP64 holds 1e-12 to 100 steps and FP32 1e-5. Over T = 5 the
+    Allen-Cahn growth rate f'(0) = 1 amplifies rounding (e^5 ~ 150): FP32 has measured up to 2.9e-5 (rel L2) /
+    4.8e-5 (rel Linf) and FP64 6.8e-13 / 1.04e-12, so the 500-step bounds are about twice those: 1e-4 and
+    2e-12."""
     from paper_2209_11922_gb300.etd import Plan
     w = inputs.AC3D_64
     U0, ref = _ref3d(steps)

@@ -168,7 +168,9 @@ def test_example53_whole_run_keeps_the_max_bound_and_decays_the_energy():
             assert m["status"] == 0
             E.append(m["energy"])
             sup.append(m["maxabs"])
-    assert max(sup) <= g
+    # the bound holds in exact arithmetic; the converged phases sit at gamma itself, where FP64
+    # rounding of the transforms leaves values a few ulp either side (1e-14 relative: ~90 ulp)
+    assert max(sup) <= g * (1 + 1e-14)
     assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:]))
     assert sup[-1] > 0.95 * g          # the phases have separated
     assert E[-1] < 0.5 * E[0]
