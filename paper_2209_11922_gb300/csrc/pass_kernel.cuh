@@ -398,9 +398,11 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     default: break;
   }
   if (op == OP_RK1S || op == OP_S1S) s0 = 1;
-  // the spectral result that a pass stores after its stage epilogue (out1): P (S1, S1S, in b1) or U~+
-  // (RK1S, S2S, in b0, before the closing DST)
-  const int spec_out = (op == OP_S1 || op == OP_S1S) ? 1 : ((op == OP_RK1S || op == OP_S2S) ? 0 : -1);
+  // Second outputs, stored with the first at the end from b1: P (S1, S1S: b1 is not touched after the
+  // stage epilogue) and U~+ (RK1S, S2S: the stage epilogue writes its result to b1 as well, whose
+  // contents, N0~ or P, it no longer needs, before the closing DST of b0).
+  const bool out1_b1 = (op == OP_S1 || op == OP_S1S || op == OP_RK1S || op == OP_S2S);
+  const bool mirror = (op == OP_RK1S || op == OP_S2S);
   C* const b0p = b0 + p * LP;
   C* const b1p = b1 + p * LP;
   C* const scrp = scr + p * (TPP > 32 ? TPP / 32 : 1);
@@ -425,7 +427,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
         out[t] = E * uv[t] + tau * p1 * wv[t];
       }
       b0p[L::at(j)] = C{out[0], out[1]};
-      return w;
+      return mirror ? C{out[0], out[1]} : w;   // (written to b1, the buffer transformed last)
     }
     if (kind == EPI_S1) {
       const T cjj = cj[j];
@@ -454,6 +456,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       stage_phi12<T>(zeta, E, act, p1, p2, rz);
       out[t] = pv[t] + (tau * inv_c2) * p2 * wv[t];
     }
+    if (mirror) b1p[L::at(j)] = C{out[0], out[1]};
     return C{out[0], out[1]};
   };
 
@@ -503,10 +506,14 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
             bpk[aj] = C{pe[0] * ej[j] * u.x + cf4[c].y * w.x, pe[1] * ej[j] * u.y + cf4[c].w * w.y};
           } else if (kind == EPI_RK1) {  // tau phi1(-z) per mode
             const C u = b0p[aj];
-            b0p[aj] = C{pe[0] * ej[j] * u.x + cf2[c].x * w.x, pe[1] * ej[j] * u.y + cf2[c].y * w.y};
+            const C r{pe[0] * ej[j] * u.x + cf2[c].x * w.x, pe[1] * ej[j] * u.y + cf2[c].y * w.y};
+            b0p[aj] = r;
+            if (mirror) b1p[aj] = r;
           } else {                       // S2: tau phi2(-z)/c2 per mode; P in the second buffer
             const C pp = b1p[aj];
-            bpk[aj] = C{pp.x + cf2[c].x * w.x, pp.y + cf2[c].y * w.y};
+            const C r{pp.x + cf2[c].x * w.x, pp.y + cf2[c].y * w.y};
+            bpk[aj] = r;
+            if (mirror) b1p[aj] = r;
           }
         }
       }
@@ -527,7 +534,6 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
       C* const scrs[2] = {scrp, scrp};   // unused by the odd-extension variant
       dst_pairs<T, N, VAR, 2>(bps, tw, sn, l, scrs, A.sc);
       stage_epilogue(epi[1], b1p);
-      if (op == OP_S1) store_tile(b1, A.out1);
       s0 = 2;
     }
   }
@@ -549,11 +555,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     }
     const React<T> rx{op == OP_REACT && s == 1 && !logr, A.flin, A.fcub};
     dst_pair<T, N, VAR>(bp, tw, sn, l, scrp, A.sc, rx);
-    if (kind != EPI_PLAIN) {
-      stage_epilogue(kind, bp);
-      // (the closing DST of b0 reads the buffer before its first barrier and writes after it)
-      if (spec_out >= 0) store_tile(spec_out ? b1 : b0, A.out1);
-    }
+    if (kind != EPI_PLAIN) stage_epilogue(kind, bp);
   }
 
   if (op == OP_REACT && A.src_gx) {
@@ -578,6 +580,7 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
   griddep_launch_dependents();
   if (op == OP_EXIT) store_dense(b0, A.out0);
   else store_tile(b0, A.out0);
+  if (out1_b1) store_tile(b1, A.out1);
 }
 
 // One plan: the launch covers the tiles of one field.
