@@ -128,8 +128,8 @@ struct etd_plan_s {
   void* tables = nullptr;
   const void* tw[3] = {};
   const void* stw[3] = {};   // twiddle tables of the split-radix kernels (split axes)
-  float* coef = nullptr;     // per-mode stage coefficients of the split last-axis passes (2D FP32)
-  size_t coef_s1 = 0, coef_s2 = 0, coef_rk1 = 0;   // float offsets of the S1, S2, RK1 tables
+  void* coef = nullptr;      // per-mode stage coefficients of the last-axis passes of 2D plans (plan's dtype)
+  size_t coef_s1 = 0, coef_s2 = 0, coef_rk1 = 0;   // element offsets of the S1, S2, RK1 tables
   const void* sn[3] = {};
   const void* zeta[3] = {};
   const void* ex[3] = {};
@@ -219,9 +219,10 @@ etd_status make_split_launch(etd_plan_s* pl, int op, int axis, const void* in0, 
   }
   a.P = P;
   if (pl->coef) {
-    if (op == OP_S1) a.coef = pl->coef + pl->coef_s1;
-    else if (op == OP_S2) a.coef = pl->coef + pl->coef_s2;
-    else if (op == OP_RK1) a.coef = pl->coef + pl->coef_rk1;
+    const float* cf = static_cast<const float*>(pl->coef);
+    if (op == OP_S1) a.coef = cf + pl->coef_s1;
+    else if (op == OP_S2) a.coef = cf + pl->coef_s2;
+    else if (op == OP_RK1) a.coef = cf + pl->coef_rk1;
   }
   const int nf = (op == OP_S1 || op == OP_RK1) ? 2 : 1;
   L.fn = fn;
@@ -265,12 +266,11 @@ etd_status make_launch(etd_plan_s* pl, int op, int axis, const void* in0, const 
   a.tw = static_cast<const T*>(pl->tw[axis]);
   a.sn = static_cast<const T*>(pl->sn[axis]);
   a.sc = (T)pl->sc[axis];
-  if constexpr (sizeof(T) == 4) {
-    if (pl->coef && pl->ndim == 2 && axis == 1) {
-      if (op == OP_S1 || op == OP_S1S) a.coef = pl->coef + pl->coef_s1;
-      else if (op == OP_S2 || op == OP_S2S) a.coef = pl->coef + pl->coef_s2;
-      else if (op == OP_RK1 || op == OP_RK1S) a.coef = pl->coef + pl->coef_rk1;
-    }
+  if (pl->coef && pl->ndim == 2 && axis == 1) {
+    const T* cf = static_cast<const T*>(pl->coef);
+    if (op == OP_S1 || op == OP_S1S) a.coef = cf + pl->coef_s1;
+    else if (op == OP_S2 || op == OP_S2S) a.coef = cf + pl->coef_s2;
+    else if (op == OP_RK1 || op == OP_RK1S) a.coef = cf + pl->coef_rk1;
   }
   const bool two = (op == OP_RK1 || op == OP_S1 || op == OP_S2 || op == OP_RK1S || op == OP_S1S || op == OP_S2S);
   const int maxp = 512 / k->tpp > 0 ? 512 / k->tpp : 1;
@@ -926,6 +926,7 @@ void phi12_fp64(double z, double& p1, double& p2) {
 // kernels read them), computed in FP64 from zeta = tau D (mu_x + mu_y) with the closed-form 1D rates (those of append_axis_tables) and
 // rounded once to FP32; layouts as documented for PassArgs::coef (the exponentials e^{-z}, e^{-c2 z} are
 // products of the per-axis tables).
+template <class T>
 etd_status upload_coef_tables(etd_plan_s* pl) {
   const int nx = pl->nx, ny = pl->ny;
   const size_t modes = (size_t)nx * ny;
@@ -938,7 +939,7 @@ etd_status upload_coef_tables(etd_plan_s* pl) {
   };
   for (int i = 0; i < nx; ++i) mx[i] = mu(i, nx, pl->h[0]);
   for (int j = 0; j < ny; ++j) my[j] = mu(j, ny, pl->h[1]);
-  std::vector<float> h;
+  std::vector<T> h;
   if (pl->scheme == 2) {
     pl->coef_s1 = 0;
     pl->coef_s2 = 2 * modes;
@@ -950,9 +951,9 @@ etd_status upload_coef_tables(etd_plan_s* pl) {
         double p1, p2, p1c, p2c;
         phi12_fp64(-z, p1, p2);
         phi12_fp64(-c2 * z, p1c, p2c);
-        h[2 * m + 0] = (float)(c2 * tau * p1c);
-        h[2 * m + 1] = (float)(tau * (p1 - p2 / c2));
-        h[2 * modes + m] = (float)(tau * p2 / c2);
+        h[2 * m + 0] = (T)(c2 * tau * p1c);
+        h[2 * m + 1] = (T)(tau * (p1 - p2 / c2));
+        h[2 * modes + m] = (T)(tau * p2 / c2);
       }
   } else {
     pl->coef_rk1 = 0;
@@ -962,11 +963,11 @@ etd_status upload_coef_tables(etd_plan_s* pl) {
         const size_t m = (size_t)j * nx + i;
         double p1, p2;
         phi12_fp64(-tauD * (mx[i] + my[j]), p1, p2);
-        h[m] = (float)(tau * p1);
+        h[m] = (T)(tau * p1);
       }
   }
-  ETD_CUDA(cudaMalloc(&pl->coef, h.size() * sizeof(float)));
-  ETD_CUDA(cudaMemcpy(pl->coef, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  ETD_CUDA(cudaMalloc(&pl->coef, h.size() * sizeof(T)));
+  ETD_CUDA(cudaMemcpy(pl->coef, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   return ETD_OK;
 }
 
@@ -1671,9 +1672,13 @@ etd_status etd_plan_create(etd_plan* out, int ndim, const int64_t* N, const doub
   for (int f = 0; f < nf; ++f) pl->F[f] = static_cast<char*>(pl->ws) + f * fbytes;
   etd_status st = (pl->elem == 4) ? upload_tables<float>(pl) : upload_tables<double>(pl);
   if (st != ETD_OK) return bail(st);
-  // per-mode phi-function weights of the y passes of 2D FP32 plans on the FFT routes (at most 64 MiB)
-  if (ndim == 2 && pl->elem == 4 && !pl->periodic && !gemm && pl->nfield * (pl->scheme == 2 ? 12 : 4) <= ((size_t)64 << 20)) {
-    if ((st = upload_coef_tables(pl)) != ETD_OK) return bail(st);
+  // per-mode phi-function weights of the y passes of 2D plans on the FFT routes (at most 64 MiB): FP32
+  // plans, and FP64 plans whose y axis runs the FP64 operation-fixed kernels (N = 1024), which read them
+  const size_t coef_bytes = pl->nfield * (pl->scheme == 2 ? 3 : 1) * (size_t)pl->elem;
+  if (ndim == 2 && !pl->periodic && !gemm && coef_bytes <= ((size_t)64 << 20)) {
+    if (pl->elem == 4) st = upload_coef_tables<float>(pl);
+    else if (pl->odd[1] == V_REC && N[1] == 1024) st = upload_coef_tables<double>(pl);
+    if (st != ETD_OK) return bail(st);
   }
   if (gemm) {
     pl->gemm = 1 + (o.route == ETD_ROUTE_GEMM_TF32 ? GR_TF32 : GR_BF16X3);

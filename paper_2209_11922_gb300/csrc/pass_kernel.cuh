@@ -118,6 +118,39 @@ template <class T, int N, int VAR> constexpr bool TABLES_ON() { return sizeof(T)
 // (staged before the dependency wait; the host passes no tables where a launch cannot stage them);
 // longer axes read the tables from global memory.
 template <class T, int N, int VAR> constexpr bool TABLES_STAGED() { return TABLES_ON<T, N, VAR>() && N <= 1536; }
+// Shapes with kernels per operation for the passes of a time step (REACT, TRANSFORM, RK1S, S1S, S2S):
+// the FP32 lengths of the large 2D and 3D workloads and of batches of meshes from 64 to 384, and the FP64
+// length of the 2D workloads (N = 1024).
+template <class T, int N, int VAR> constexpr bool pass_op_kernels() {
+  return (sizeof(T) == 4 &&
+          ((VAR == V_ODD && (N == 1024 || N == 2048)) ||
+           (VAR == V_REC && (N == 64 || N == 96 || N == 128 || N == 192 || N == 256 || N == 384)) ||
+           (VAR == V_HART && N == 128))) ||
+         (sizeof(T) == 8 && VAR == V_REC && N == 1024);
+}
+// FP64: the operation-fixed kernels (the 2D FP64 workloads' axis length) read the tables from global memory.
+template <class T, int N, int VAR> constexpr bool TABLES_ANY() {
+  return TABLES_ON<T, N, VAR>() || (sizeof(T) == 8 && pass_op_kernels<T, N, VAR>());
+}
+
+// Per-mode weights of one pencil pair at table position m: S1 four values (two per pencil), S2 and RK1
+// two (one per pencil), loaded as 16-byte vectors.
+template <class T> struct PairWeights;
+template <> struct PairWeights<float> {
+  using W4 = float4;
+  using W2 = float2;
+  static __device__ __forceinline__ W4 ld4(const float* p, size_t m) { return reinterpret_cast<const float4*>(p)[m]; }
+  static __device__ __forceinline__ W2 ld2(const float* p, size_t m) { return reinterpret_cast<const float2*>(p)[m]; }
+};
+template <> struct PairWeights<double> {
+  struct W4 { double x, y, z, w; };
+  using W2 = double2;
+  static __device__ __forceinline__ W4 ld4(const double* p, size_t m) {
+    const double2 a = reinterpret_cast<const double2*>(p)[2 * m], b = reinterpret_cast<const double2*>(p)[2 * m + 1];
+    return W4{a.x, a.y, b.x, b.y};
+  }
+  static __device__ __forceinline__ W2 ld2(const double* p, size_t m) { return reinterpret_cast<const double2*>(p)[m]; }
+};
 template <class T, int N, int VAR> constexpr int pass_min_blocks() {
   // 3 x 2^k lengths above 48 keep 128 registers (their radix-3/12 stages spill at 64), except the
   // recurrence plan of N = 96 (radices 4, 3, 8), which fits
@@ -460,20 +493,22 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
     return C{out[0], out[1]};
   };
 
-  // FP32 2D plans: the phi-function weights of the stage combination come from per-mode tables of FP64
-  // values rounded once (A.coef, [y mode][x mode]; e^{-z}, e^{-c2 z} are products of the per-axis
-  // factors), with every table load of a chunk of positions issued before the first use. Same
+  // 2D plans: the phi-function weights of the stage combination come from per-mode tables of FP64
+  // values (FP32 plans: rounded once) (A.coef, [y mode][x mode]; e^{-z}, e^{-c2 z} are products of the
+  // per-axis factors), with every table load of a chunk of positions issued before the first use. Same
   // effect on the buffers as the epilogue above.
-  // Compiled into the kernels with the full register budget only; the others evaluate the weights.
-  constexpr bool TABLES = TABLES_ON<T, N, VAR>();
+  // Compiled into the FP32 kernels with the full register budget and the FP64 operation-fixed kernels
+  // only; the others evaluate the weights.
+  constexpr bool TABLES = TABLES_ANY<T, N, VAR>();
   auto table_epilogue = [&](int kind, C* bpk) {
     if constexpr (TABLES) {
-      constexpr int CNT = (N + TPP - 1) / TPP, CH = 4;
+      constexpr int CNT = (N + TPP - 1) / TPP, CH = sizeof(T) == 4 ? 4 : 2;
+      using PW = PairWeights<T>;
       const size_t col = (size_t)x0 + 2 * p;
 #pragma unroll
       for (int c0 = 0; c0 < CNT; c0 += CH) {
-        float4 cf4[CH];
-        float2 cf2[CH];
+        typename PW::W4 cf4[CH];
+        typename PW::W2 cf2[CH];
         if constexpr (TABLES_STAGED<T, N, VAR>()) {   // staged chunk-major: S1 one pair per chunk, else two
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
@@ -489,8 +524,8 @@ __device__ __forceinline__ void pass_body(const PassArgs<T>& A, const int tile) 
             const int j = l + (c0 + c) * TPP;
             if (c0 + c < CNT && j < N) {
               const size_t m = ((size_t)j * A.nx + col) / 2;
-              if (kind == EPI_S1) cf4[c] = reinterpret_cast<const float4*>(A.coef)[m];
-              else cf2[c] = reinterpret_cast<const float2*>(A.coef)[m];
+              if (kind == EPI_S1) cf4[c] = PW::ld4(A.coef, m);
+              else cf2[c] = PW::ld2(A.coef, m);
             }
           }
         }
@@ -595,15 +630,6 @@ __global__ void __launch_bounds__(512, pass_min_blocks<T, N, VAR>()) pass_kernel
   pass_body<T, N, VAR, OPC>(A, (int)blockIdx.x);
 }
 
-// Shapes with kernels per operation for the passes of a time step (REACT, TRANSFORM, RK1, S1, S2):
-// the FP32 lengths of the large 2D and 3D workloads and of batches of meshes from 64 to 384.
-template <class T, int N, int VAR> constexpr bool pass_op_kernels() {
-  return sizeof(T) == 4 &&
-         ((VAR == V_ODD && (N == 1024 || N == 2048)) ||
-          (VAR == V_REC && (N == 64 || N == 96 || N == 128 || N == 192 || N == 256 || N == 384)) ||
-          (VAR == V_HART && N == 128));
-}
-
 // Batches: one launch covers the tiles of many independent problems whose transformed axis has
 // length N. CTA b works on tile map[b].y of the problem described by descs[map[b].x]; entry and exit
 // passes take the caller's field pointer from user[descs[.].user_slot].
@@ -667,11 +693,13 @@ template <class T, int N, int VAR> KernelInfo kernel_info() {
     k.fn_op[OP_RK1S] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_RK1S>);
     k.fn_op[OP_S1S] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S1S>);
     k.fn_op[OP_S2S] = reinterpret_cast<const void*>(&pass_kernel_op<T, N, VAR, OP_S2S>);
-    // batches are 2D: TRANSFORM only at entry (the generic kernel)
+    // batches (FP32) are 2D: TRANSFORM only at entry (the generic kernel)
+    if constexpr (sizeof(T) == 4) {
     k.fn_batched_op[OP_REACT] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_REACT>);
     k.fn_batched_op[OP_RK1S] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_RK1S>);
     k.fn_batched_op[OP_S1S] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S1S>);
     k.fn_batched_op[OP_S2S] = reinterpret_cast<const void*>(&pass_kernel_batched_op<T, N, VAR, OP_S2S>);
+    }
   }
   radix_list(k.radix, typename L::Plan::R{});
   return k;
